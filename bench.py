@@ -1,0 +1,471 @@
+#!/usr/bin/env python
+"""Throughput of the yarn BYSDF hot path on GB300.
+
+Default step (workload "eval+sample+pdf-8mat-2^24"): 2^24 hit records over 8
+yarn materials, each record evaluated at omega_o (f and pdf) and importance
+sampled from two uniform numbers (direction, weight, pdf), in the fused
+persistent kernel.  value = records per second over all ranks (weak scaling:
+each rank owns its own 2^24 records); inputs are larger than L2.
+
+Also reported (same JSON line): the other workloads (near-field eval,
+multi-scale, 256-material batched with a CUDA graph, forward + backward), the
+plain per-material-launch form, the end-to-end rate with host buffers, the
+roofline of the fused kernel, and the FP64 oracle on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_12724_gb300 import inputs as I  # noqa: E402
+
+METRIC = "BYSDF evals/sec (fwd, fwd+bwd) on 1 GB300, % FP32/SFU roofline, vs plain, ≤1e-4 rel err"
+UNIT = "records/s"
+MAIN_CFG = 2
+
+# Algorithmic work per record, counted by the FP64 oracle's operation-counting
+# scalar on 4096 records of each workload (oracle/count_ops.py): FP32 flops
+# (adds + multiplies) and XU ops (divisions, square roots, transcendentals).
+OPS = {
+    1: dict(eval=(461.2, 63.5)),
+    2: dict(eval=(499.9, 69.1), fused=(673.5, 88.1)),
+    3: dict(eval=(2902.8, 431.6), fused=(3082.3, 451.1)),
+    4: dict(eval=(541.0, 75.0), fused=(720.8, 94.6)),
+    5: dict(eval=(397.7, 54.2)),
+}
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
+XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM
+SM_MAX_MHZ = 2070.0
+
+
+def peaks(sm_count: int, mhz: float):
+    return dict(fp32_tflops=sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+                xu_tops=sm_count * XU_LANES_PER_SM * mhz * 1e6 / 1e12)
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6),
+                              ("sw_thermal_slowdown", 7), ("sw_power_cap", 8)):
+                if r[col].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ------------------------------------------------------------ distributed --
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def dist_max(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ------------------------------------------------------------ CPU oracle --
+def cpu_oracle_rate(cfg: int, target_s: float = 8.0, max_records: int = 1 << 21):
+    """The FP64 oracle, as it stands, on this host's cores: eval at omega_o
+    (with pdf) plus one sample per record, on a bounded prefix of the
+    workload sized to take about target_s."""
+    import oracle
+    threads = os.cpu_count() or 1
+    mats = I.materials(cfg)
+    n = 1 << 14
+    while True:
+        rec = I.records(cfg, 0, n)
+        t0 = time.perf_counter()
+        oracle.eval_records(mats, rec, threads=threads)
+        oracle.sample_records(mats, rec, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or n >= max_records:
+            return dict(value=n / dt, unit=UNIT, cores=threads, kind="oracle",
+                        sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, "
+                               f"eval(+pdf) and one sample each, FP64, {threads} threads",
+                        seconds=dt, records=n)
+        n = min(max_records, int(n * min(16.0, max(2.0, target_s / max(dt, 1e-3)))))
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, each step a
+    bounded sample of the workload."""
+    import oracle
+    threads = os.cpu_count() or 1
+    cfg = MAIN_CFG
+    mats = I.materials(cfg)
+    n = 1 << 16
+    rec = I.records(cfg, 0, n)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.eval_records(mats, rec, threads=threads)
+        oracle.sample_records(mats, rec, threads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = n * len(times) / tot
+    sample = (f"first {n} records of workload {I.WORKLOAD_NAME[cfg]} per step, eval(+pdf) and "
+              f"one sample each, FP64, {threads} threads")
+    line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * tot / len(times),
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic",
+                config=dict(workload=I.WORKLOAD_NAME[cfg], records_per_step=n, materials=len(mats)),
+                cpu_baseline=dict(value=val, unit=UNIT, cores=threads, kind="oracle", sample=sample),
+                e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU ----
+def timed(fn, steps, warmup, stream=None):
+    """Mean milliseconds per call with CUDA events on the launching stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    st = stream or torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        starts[k].record(st)
+        fn()
+        ends[k].record(st)
+    torch.cuda.synchronize()
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return sum(per) / len(per), per
+
+
+def workload_device(api, cfg, rank):
+    seed = None if rank == 0 else I.SEED_BASE + cfg + 1000 * rank
+    rec = I.records(cfg, seed=seed)
+    seg = I.seg_offsets(cfg, seed=seed)
+    d = api.records_to_device(rec, "cuda", seg)
+    return rec, d, seg
+
+
+def sorted_copy(d, n_mat):
+    """Records permuted into material order (for the plain per-material form)."""
+    import torch
+    order = torch.argsort(d["mat_id"], stable=True)
+    out = {}
+    for k, t in d.items():
+        out[k] = t[..., order].contiguous() if t.shape[-1] == order.numel() else t
+    counts = torch.bincount(d["mat_id"].long(), minlength=n_mat).cpu().numpy()
+    seg = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return out, seg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--main-only", action="store_true", help="skip the other workloads")
+    ap.add_argument("--profile", action="store_true",
+                    help="main workload only, no clocks/e2e/CPU baseline (for ncu)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    from paper_2401_12724_gb300 import _native as N
+    from paper_2401_12724_gb300 import api
+
+    torch.cuda.set_device(local)
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+
+    # ---------------------------------------------- main workload (fused) --
+    cfg = MAIN_CFG
+    mats = I.materials(cfg)
+    M = api.Materials(mats)
+    rec, d, _ = workload_device(api, cfg, rank)
+    n = int(d["h"].shape[0])
+    out = api.alloc_fused(n, "cuda")
+    step = lambda: api.eval_sample_pdf(M, d, out=out)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    if not args.profile:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if not args.profile else None
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms_total = ev[0].elapsed_time(ev[-1])
+    ms_total = dist_max(ms_total)
+    ms_step = ms_total / args.steps
+    value = ws * n * args.steps / (ms_total / 1e3)
+    err = M.workspace_error()
+    if err:
+        raise RuntimeError(f"device-side error word {err:#x} during the timed steps")
+
+    if rank != 0:
+        return
+    # roofline of the fused kernel (its launch is one plan kernel + the fused
+    # kernel; the step time bounds the fused kernel's time from above)
+    fl, xu = OPS[cfg]["fused"]
+    t_launch = sum(per_launch) / len(per_launch) / 1e3
+    ach_fp32 = fl * n / t_launch / 1e12
+    ach_xu = xu * n / t_launch / 1e12
+    pk = peaks(sm_count, SM_MAX_MHZ)
+    frac_fp32 = ach_fp32 / pk["fp32_tflops"]
+    frac_xu = ach_xu / pk["xu_tops"]
+    if frac_fp32 >= frac_xu:
+        roof = dict(bound="alu", pipe="fp32", achieved=ach_fp32, peak=pk["fp32_tflops"],
+                    unit="TFLOP/s", frac=frac_fp32)
+    else:
+        roof = dict(bound="alu", pipe="xu", achieved=ach_xu, peak=pk["xu_tops"], unit="Top/s",
+                    frac=frac_xu)
+    roof.update(traffic=None, peak_basis=f"{sm_count} SMs x lanes x {SM_MAX_MHZ:.0f} MHz",
+                pipes=dict(fp32=dict(achieved_tflops=ach_fp32, frac=frac_fp32,
+                                     flops_per_record=fl),
+                           xu=dict(achieved_tops=ach_xu, frac=frac_xu, ops_per_record=xu)),
+                algorithmic_bytes_per_record=48 + 46)
+    if clk:
+        pm = peaks(sm_count, clk["sm_mhz"])
+        roof["frac_at_measured_clock"] = max(ach_fp32 / pm["fp32_tflops"], ach_xu / pm["xu_tops"])
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=I.WORKLOAD_NAME[cfg], records=n, materials=len(mats),
+                            step="fused eval(+pdf at wo) + one importance sample per record",
+                            l2="inputs larger than L2 (~0.8 GB of records per step)",
+                            launch=M.launch_config(N.OP_FUSED),
+                            parallelism=f"records sharded, {ws} rank(s)"),
+                roofline=roof, gpu_launches=2 * args.steps)
+    if clk:
+        line["clocks"] = clk
+
+    if not args.profile:
+        # ------------------------------------------ end to end, host buffers --
+        hin = api.pinned_records(rec)
+        hout = api.pinned_fused_outputs(n)
+        pipe = api.HostPipeline(M, chunk=1 << 21)
+        pipe.run(hin, hout)
+        torch.cuda.synchronize()
+        e2e_steps = max(3, args.steps // 4)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pipe.run(hin, hout)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        bi, bo = api.HostPipeline.bytes_per_record(hin, hout)
+        line["e2e"] = dict(value=n * e2e_steps / dt, unit=UNIT,
+                           h2d_bytes_per_step=int(bi * n), d2h_bytes_per_step=int(bo * n),
+                           chunks=math.ceil(n / (1 << 21)))
+        del hin, hout, pipe
+
+        # ------------------------------------------ plain form, same records --
+        ds, seg = sorted_copy(d, len(mats))
+        po = api.alloc_fused(n, "cuda")
+        plain_out = dict(f=po["f"], wo=po["wo"], weight=po["weight"], pdf=po["pdf"],
+                         status=po["status"])
+
+        def plain_step():
+            api.plain(N.OP_EVAL, M, ds, seg, out=plain_out)
+            api.plain(N.OP_SAMPLE, M, ds, seg, out=plain_out)
+            api.plain(N.OP_PDF, M, ds, seg, out=plain_out)
+        ms_plain, _ = timed(plain_step, max(3, args.steps // 2), 2)
+        # the same three ops as separate persistent calls (no fusion)
+        sep = lambda: (api.eval(M, d, out=out), api.sample(M, d, out=dict(  # noqa: E731
+            wo=out["wo"], weight=out["weight"], pdf=out["pdf_s"], lobe_status=out["lobe_status"])),
+            api.pdf(M, d, out=out))
+        ms_sep, _ = timed(sep, max(3, args.steps // 2), 2)
+        line["vs_plain"] = dict(plain_records_per_s=n / (ms_plain / 1e3),
+                                separate_persistent_records_per_s=n / (ms_sep / 1e3),
+                                fused_speedup_vs_plain=ms_plain / ms_step,
+                                plain_launches_per_step=3 * len(mats))
+        del ds, po, plain_out
+        del d, out
+        torch.cuda.empty_cache()
+
+        if not args.main_only:
+            line["workloads"] = other_workloads(api, N, torch, args, sm_count)
+        line["cpu_baseline"] = cpu_oracle_rate(cfg)
+    print(json.dumps(line), flush=True)
+
+
+def other_workloads(api, N, torch, args, sm_count):
+    res = {}
+    steps = max(3, args.steps // 2)
+    # near-field eval, 1 material, 65,536 records
+    mats = I.materials(1)
+    M = api.Materials(mats)
+    _, d, _ = workload_device(api, 1, 0)
+    n = int(d["h"].shape[0])
+    o = dict(f=torch.empty(3, n, device="cuda"), pdf=torch.empty(n, device="cuda"),
+             status=torch.empty(n, dtype=torch.uint8, device="cuda"))
+    ms, _ = timed(lambda: api.eval(M, d, out=o), steps * 4, 3)
+    res[I.WORKLOAD_NAME[1]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
+                                   roofline_frac=frac(OPS[1]["eval"], n, ms, sm_count))
+    # multi-scale: fused eval + sample
+    mats = I.materials(3)
+    M = api.Materials(mats)
+    _, d, _ = workload_device(api, 3, 0)
+    n = int(d["h"].shape[0])
+    o = api.alloc_fused(n, "cuda")
+    ms, _ = timed(lambda: api.eval_sample_pdf(M, d, out=o), steps, 2)
+    res[I.WORKLOAD_NAME[3]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
+                                   roofline_frac=frac(OPS[3]["fused"], n, ms, sm_count))
+    del d, o
+    torch.cuda.empty_cache()
+    # batched heterogeneous: 256 materials, Zipf counts, one persistent
+    # material-sorted launch per op captured in a CUDA graph, vs plain
+    mats = I.materials(4)
+    M = api.Materials(mats)
+    rec4, d, seg = workload_device(api, 4, 0)
+    del rec4
+    n = int(d["h"].shape[0])
+    o = api.alloc_fused(n, "cuda")
+    tuned = api.autotune(M, N.OP_FUSED, d, out=o)
+    api.eval_sample_pdf(M, d, out=o)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        api.eval_sample_pdf(M, d, out=o, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        api.eval_sample_pdf(M, d, out=o)
+    ms_graph, _ = timed(g.replay, steps, 2)
+    po = dict(f=o["f"], wo=o["wo"], weight=o["weight"], pdf=o["pdf"], status=o["status"])
+
+    def plain_step():
+        api.plain(N.OP_EVAL, M, d, seg, out=po)
+        api.plain(N.OP_SAMPLE, M, d, seg, out=po)
+        api.plain(N.OP_PDF, M, d, seg, out=po)
+    ms_plain, _ = timed(plain_step, max(2, steps // 2), 1)
+    res[I.WORKLOAD_NAME[4]] = dict(records_per_s=n / (ms_graph / 1e3), ms=ms_graph, records=n,
+                                   autotuned=tuned, plain_records_per_s=n / (ms_plain / 1e3),
+                                   speedup_vs_plain=ms_plain / ms_graph,
+                                   roofline_frac=frac(OPS[4]["fused"], n, ms_graph, sm_count))
+    del d, o, po, g
+    torch.cuda.empty_cache()
+    # forward + backward, 64 materials, material-sorted
+    mats = I.materials(5)
+    M = api.Materials(mats)
+    rec5, d, seg = workload_device(api, 5, 0)
+    n = int(d["h"].shape[0])
+    gf = torch.from_numpy(rec5["g"]).cuda()
+    del rec5
+    f = torch.empty(3, n, device="cuda")
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gp = torch.empty(64, 8, device="cuda")
+
+    def fwd_bwd():
+        api.eval(M, d, with_pdf=False, out=dict(f=f, status=st))
+        api.eval_backward(M, d, gf, out=gp)
+    ms_fb, _ = timed(fwd_bwd, max(3, steps // 2), 1)
+    ms_f, _ = timed(lambda: api.eval(M, d, with_pdf=False, out=dict(f=f, status=st)), steps, 2)
+    res[I.WORKLOAD_NAME[5]] = dict(records_per_s=n / (ms_fb / 1e3), ms=ms_fb, records=n,
+                                   forward_only_records_per_s=n / (ms_f / 1e3),
+                                   roofline_frac_forward=frac(OPS[5]["eval"], n, ms_f, sm_count))
+    return res
+
+
+def frac(ops, n, ms, sm_count):
+    fl, xu = ops
+    pk = peaks(sm_count, SM_MAX_MHZ)
+    t = ms / 1e3
+    return max(fl * n / t / 1e12 / pk["fp32_tflops"], xu * n / t / 1e12 / pk["xu_tops"])
+
+
+if __name__ == "__main__":
+    main()

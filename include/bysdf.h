@@ -1,0 +1,238 @@
+/*
+ * libbysdf -- batched yarn-level BYSDF on the GPU (sm_103a).
+ *
+ * The bidirectional yarn scattering distribution function of "A Multi-scale
+ * Yarn Appearance Model with Fiber Details" (Khattar et al.), evaluated,
+ * sampled and differentiated at ray--yarn hit records:
+ *   - implicit ply geometry by the iterated cross-section trace (Sec. 3.4),
+ *   - implicit fibers from 1D maps (Sec. 3.5.1),
+ *   - ply and fiber shadowing G_p, G_f (Sec. 4.1.4),
+ *   - the four lobes f_x^S, f_y^S, f_x^B, f_y^B (Sec. 4.1, Eqs. 1-6) with the
+ *     attenuation tau^{N_i} (Eq. 4),
+ *   - importance sampling and its pdf (Sec. 4.1.5),
+ *   - near / multi-scale / far-field selection by pixel coverage
+ *     (Sec. 4.2, Eqs. 7-11; Sec. 5.3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Frame: yarn-local at the hit; x = reference normal, y = T x N_ref, z = yarn
+ * tangent.  Lengths in units of the yarn radius of the material.  Directions
+ * are unit float32 3-vectors pointing AWAY from the hit; omega_i is the
+ * camera-side direction.  Outputs f are cosine-weighted, f(wi, wo) |wo . n|,
+ * with n the shading normal at the hit, so that a renderer multiplies them by
+ * the incident radiance directly; pdf is a solid-angle density of wo.
+ *
+ * Buffers: every per-record buffer is DEVICE memory owned by the caller,
+ * float32 (int32 ids, uint8 status), structure-of-arrays: a 3-vector plane
+ * argument points to 3*n floats laid out [x[0..n), y[0..n), z[0..n)].  Every
+ * buffer must be 16-byte aligned.  Calls are asynchronous on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and allocate no memory: the
+ * caller provides a workspace of at least bysdf_workspace_size() bytes, which
+ * must not be shared by calls that may run concurrently.
+ *
+ * Per-record status (uint8): 0 ok; 1 no ply hit (the ray passes through the
+ * yarn, f = 0, pdf = 0); 2 invalid input (non-finite value, |h| > 1, a
+ * direction whose squared norm is off by more than 1e-3, material id out of
+ * range, negative ratio, random number outside [0, 1)); 3 invalid sample
+ * (the sampled direction left the lobe's support, e.g. total internal
+ * reflection).  Sampling writes lobe << 4 | status, lobe 0 = f_x^S
+ * (reflection), 1 = f_y^S (transmission), 2 = f_x^B, 3 = f_y^B.
+ *
+ * Return codes: 0 ok; negative on a host-side error, in which case nothing
+ * was launched (bysdf_last_error() describes it).
+ */
+#ifndef BYSDF_H
+#define BYSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BYSDF_OK 0
+#define BYSDF_E_ARG (-1)         /* null/misaligned pointer, bad size, bad descriptor */
+#define BYSDF_E_CUDA (-2)        /* a CUDA runtime call failed */
+#define BYSDF_E_UNSUPPORTED (-3) /* a combination this build does not run */
+#define BYSDF_E_WORKSPACE (-4)   /* workspace missing or too small */
+
+#define BYSDF_NPARAM 8 /* differentiable parameters per material, see below */
+
+/* Material descriptor (host).  Sec. 3.4 / 3.5 geometry, Sec. 4.1 appearance.
+ * Readings of quantities the paper leaves open are documented with each
+ * field; all angles in degrees. */
+typedef struct bysdf_material_desc {
+  int32_t n_plies;        /* N_p in [1, 8]; plies are equal discs inscribed in
+                             the yarn circle, touching it and each other     */
+  int32_t fibers_per_ply; /* N_f in [4, 4096]; fibers fill `packing` of a ply */
+  int32_t map_texels;     /* T in [4, 1024]: texels per fiber period of the 1D
+                             fiber maps (Sec. 3.5.1); 256 by default          */
+  int32_t trace_iters;    /* N_it in [1, 64]: cross-section updates of the ply
+                             trace (Sec. 3.4: "3-5 steps"); 5 by default      */
+  int32_t k_max;          /* K_max in [1, 64]: h nodes of a footprint that
+                             covers the yarn (Sec. 4.2); 16 by default        */
+  int32_t flags;          /* bit 0: no fiber detail (flat ply surface)        */
+  float yarn_radius;      /* R > 0                                            */
+  float ply_twist_deg;    /* helix angle of the ply centre lines              */
+  float fiber_twist_deg;  /* helix angle of the fibers about the ply axis     */
+  float eta;              /* refractive index > 1                             */
+  float albedo[3];        /* body albedo k^B (RGB), Eqs. 5-6                  */
+  float k_spec;           /* specular albedo scale: k^S = (1 - B) k_spec      */
+  float beta_deg[2];      /* GGX roughness along t_f and b_f (Eq. 2)          */
+  float body_B;           /* B in [0, 1]: body share of the energy (Sec. 4.1.5)*/
+  float body_r;           /* r in [0, 1]: reflected share of the body energy  */
+  float sigma_t;          /* extinction coefficient of Eq. 4 (per length)     */
+  float shadow_density;   /* sigma_s: G = exp(-sigma_s * occlusion) (Sec 4.1.4)*/
+  float packing;          /* fiber area fraction of a ply disc (0, 1]         */
+} bysdf_material_desc;
+
+/* Opaque material table: per-material constants and the 1D fiber normal and
+ * fiber shadowing maps, resident in device memory (Sec. 3.5.1, 4.1.4). */
+typedef struct bysdf_materials bysdf_materials;
+
+/* Hit records (device pointers; see conventions above). */
+typedef struct bysdf_hits {
+  const float* h;       /* azimuthal offset in [-1, 1] (Sec. 3.3)            */
+  const float* u;       /* azimuthal phase of the hit, radians (Sec. 3.3)    */
+  const float* v;       /* longitudinal length of the hit (Sec. 3.3)         */
+  const float* wi;      /* omega_i, 3 planes                                  */
+  const float* wo;      /* omega_o, 3 planes (eval/pdf/backward; NULL when
+                           sampling)                                          */
+  const float* ratio;   /* pixel-footprint / yarn-width ratio (Sec. 5.3):
+                           the half-width of [h1, h2] in h units; NULL or 0 =
+                           near field, >= 1 + |h| = far field (Eq. 7)         */
+  const int32_t* mat_id;     /* material of each record; NULL = material 0    */
+  const int64_t* seg_offsets;/* NULL, or n_mat + 1 offsets: records are sorted
+                                by material and material m owns
+                                [seg_offsets[m], seg_offsets[m+1]); required
+                                when the tables do not fit in shared memory  */
+} bysdf_hits;
+
+/* Launch shape of the persistent kernels (chosen by bysdf_autotune). */
+typedef struct bysdf_launch_config {
+  int32_t block;          /* threads per CTA: 128, 256 or 512               */
+  int32_t items;          /* records per lane per warp tile: 1, 2 or 4       */
+  int32_t ctas_per_sm;    /* resident CTAs per SM the grid is sized for      */
+  int32_t reserved;
+} bysdf_launch_config;
+
+enum { BYSDF_OP_EVAL = 0, BYSDF_OP_SAMPLE = 1, BYSDF_OP_PDF = 2, BYSDF_OP_FUSED = 3,
+       BYSDF_OP_BACKWARD = 4, BYSDF_NOPS = 5 };
+
+/* Version string of the library. */
+const char* bysdf_version(void);
+
+/* Description of the last host-side error of the calling thread. */
+const char* bysdf_last_error(void);
+
+/* Build the material table for n descriptors on the current device and
+ * upload it with stream-ordered copies on `stream`.  The library allocates
+ * and owns the table; release it with bysdf_destroy_materials.  The table is
+ * read-only for every call except bysdf_set_params, so it may be shared by
+ * calls on several streams.  Errors: BYSDF_E_ARG (null pointer, n < 1 or
+ * n > 65536, a descriptor field out of range), BYSDF_E_CUDA. */
+int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* stream,
+                           bysdf_materials** out);
+
+/* Release the table (synchronises the device first). */
+int bysdf_destroy_materials(bysdf_materials* m);
+
+/* Number of materials in the table. */
+int32_t bysdf_num_materials(const bysdf_materials* m);
+
+/* Replace the differentiable parameters of every material from a DEVICE
+ * array params[n_mat][8] (float32), stream-ordered:
+ *   [0..2] albedo k^B (RGB), [3] beta_t, [4] beta_b (GGX roughness, radians),
+ *   [5] ply helix angle alpha_p (radians), [6] fiber helix angle alpha_f
+ *   (radians), [7] shadow density sigma_s.
+ * The derived constants (helix rates, fiber phase rates) are recomputed on
+ * the device.  Not safe while other calls read the table. */
+int bysdf_set_params(bysdf_materials* m, const float* params, void* stream);
+
+/* Copy the current parameters to a DEVICE array [n_mat][8] (same layout). */
+int bysdf_get_params(const bysdf_materials* m, float* params, void* stream);
+
+/* Workspace bytes the calls below need for n records. */
+size_t bysdf_workspace_size(const bysdf_materials* m, int64_t n);
+
+/* Evaluate f(wi, wo) |wo . n| (RGB, 3 planes into f_rgb) and, when pdf is
+ * not NULL, the sampling density of wo (Sec. 4.1 Eqs. 1-6, Sec. 4.2 Eq. 8).
+ * status is required.  One persistent launch. */
+int bysdf_eval(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* f_rgb,
+               float* pdf, uint8_t* status, void* workspace, size_t workspace_bytes,
+               void* stream);
+
+/* Importance-sample wo from two uniform numbers per record (Sec. 4.1.5):
+ * writes wo (3 planes), weight = f |wo . n| / pdf (3 planes), pdf and
+ * lobe << 4 | status.  hits->wo is ignored.  A record without a ply hit
+ * passes through: wo = -wi, weight = 1, pdf = 0, status 1. */
+int bysdf_sample(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,
+                 const float* u1, int64_t n, float* wo, float* weight, float* pdf,
+                 uint8_t* lobe_status, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Sampling density of hits->wo (Sec. 4.1.5). */
+int bysdf_pdf(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* pdf,
+              uint8_t* status, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Eval + pdf at hits->wo and a sample from (u0, u1) in one pass over the
+ * geometry, which the three results share.  Outputs as the three calls. */
+int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,
+                          const float* u1, int64_t n, float* f_rgb, float* pdf,
+                          uint8_t* status, float* wo_s, float* weight_s, float* pdf_s,
+                          uint8_t* lobe_status_s, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Gradient of sum_i sum_c grad_f[c][i] * f_c(record i) with respect to the 8
+ * parameters of each material (layout of bysdf_set_params), accumulated
+ * into grad_params[n_mat][8] (DEVICE, zeroed by this call).  The forward pass
+ * is recomputed, not stored.  Records with status != 0 contribute nothing.
+ * deterministic != 0 reduces in a fixed order (material-sorted records with
+ * seg_offsets only; otherwise BYSDF_E_UNSUPPORTED). */
+int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                        const float* grad_f, float* grad_params, int deterministic,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* The plain form, for comparison: one launch per material over
+ * material-sorted records, one thread per record, tables read from global
+ * memory, no persistent scheduling.  seg_offsets_host: n_mat + 1 HOST
+ * offsets.  op: BYSDF_OP_EVAL, _SAMPLE or _PDF (pointers as in the calls
+ * above; unused ones may be NULL). */
+int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
+                const int64_t* seg_offsets_host, const float* u0, const float* u1,
+                int64_t n, float* f_rgb, float* wo, float* weight, float* pdf,
+                uint8_t* status, void* stream);
+
+/* Launch shape used for op (BYSDF_OP_*), per table. */
+int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_config* cfg);
+int bysdf_get_launch_config(const bysdf_materials* m, int op, bysdf_launch_config* cfg);
+
+/* Output buffers of one op, for bysdf_autotune (unused ones may be NULL). */
+typedef struct bysdf_outputs {
+  float* f_rgb;          /* eval: 3 planes                                  */
+  float* pdf;            /* eval / pdf                                      */
+  uint8_t* status;       /* eval / pdf                                      */
+  float* wo;             /* sample: 3 planes                                */
+  float* weight;         /* sample: 3 planes                                */
+  float* pdf_s;          /* sample                                          */
+  uint8_t* lobe_status;  /* sample                                          */
+  float* grad_params;    /* backward: [n_mat][8]                            */
+} bysdf_outputs;
+
+/* Time every supported launch shape of op (BYSDF_OP_EVAL, _SAMPLE, _PDF,
+ * _FUSED, _BACKWARD) on these records with CUDA events on `stream`, keep the
+ * fastest in the table for later calls and return it in *best.  Writes the
+ * op's outputs (several times).  Synchronises the stream; not capturable. */
+int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const float* u0,
+                   const float* u1, const float* grad_f, int64_t n, const bysdf_outputs* out,
+                   void* workspace, size_t workspace_bytes, void* stream,
+                   bysdf_launch_config* best);
+
+/* Device-side error word of a workspace (0 = none; bit 0: a bounded wait on
+ * a shared-memory table copy gave up).  Synchronises the stream. */
+int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BYSDF_H */

@@ -1050,11 +1050,16 @@ int orc_count_ops(const orc_material* m, int n_mat, const orc_records* r,
   for (int64_t i = 0; i < n; ++i) {
     const Rec q = read_rec(r, i, n);
     for (int k = 0; k < 6; ++k) g_ops[k] = 0.0;
-    if (valid_rec(q, n_mat, op != 1, op == 1)) {
-      if (op == 1)
+    if (valid_rec(q, n_mat, op != 1 && op != 3, op == 1)) {
+      if (op == 1) {
         sample_one(mats[q.mat], q);
-      else
+      } else if (op == 3) {
+        // the part eval and sample share: geometry and shading state
+        const Geo<Cnt> G = geometry(mats[q.mat], q);
+        if (G.status == ORC_OK) make_shade(mats[q.mat], G, q.wi);
+      } else {
         eval_one(mats[q.mat], q);
+      }
     }
     for (int k = 0; k < 6; ++k) counts[i * 6 + k] = g_ops[k];
   }

@@ -79,7 +79,8 @@ int orc_sample(const orc_material* m, int n_mat, const orc_records* r, int64_t n
 int orc_grad(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
              const double* g_rgb, double* grad, double* jac, double* f_rgb,
              int n_threads);
-/* Operation counts of one evaluation per record.  op: 0 eval, 1 sample, 2 pdf.
+/* Operation counts of one evaluation per record.  op: 0 eval (with pdf),
+ * 1 sample, 3 the geometry and shading state that eval and sample share.
  * counts: [n][6] = add/sub, mul, div, sqrt, transcendental, compare. */
 int orc_count_ops(const orc_material* m, int n_mat, const orc_records* r,
                   int64_t n, int op, double* counts);

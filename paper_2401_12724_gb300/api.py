@@ -1,0 +1,389 @@
+"""PyTorch-facing binding of libbysdf.
+
+Argument marshalling only: tensors are passed to the C ABI as raw device
+pointers and every step of the BYSDF runs in the library's CUDA kernels.
+Records are a dict of CUDA tensors: h, u, v (n,), wi, wo (3, n) float32,
+optional mat_id (n,) int32, ratio (n,) float32, seg_offsets (n_mat + 1,)
+int64.  Outputs are allocated here with torch (device memory is plumbing).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+PARAM_NAMES = ("albedo_r", "albedo_g", "albedo_b", "beta_t", "beta_b", "alpha_p", "alpha_f",
+               "sigma_s")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def desc_struct(d: dict) -> N.MaterialDesc:
+    s = N.MaterialDesc()
+    for k in ("n_plies", "fibers_per_ply", "map_texels", "trace_iters", "k_max"):
+        setattr(s, k, int(d[k]))
+    s.flags = int(d.get("flags", 0))
+    for k in ("yarn_radius", "ply_twist_deg", "fiber_twist_deg", "eta", "k_spec", "body_B",
+              "body_r", "sigma_t", "shadow_density", "packing"):
+        setattr(s, k, float(d[k]))
+    for c in range(3):
+        s.albedo[c] = float(d["albedo"][c])
+    for c in range(2):
+        s.beta_deg[c] = float(d["beta_deg"][c])
+    return s
+
+
+class Materials:
+    """Device-resident material table (bysdf_create_materials)."""
+
+    def __init__(self, descs, device=None, stream=None):
+        self.lib = N.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        self.descs = [dict(d) for d in descs]
+        arr = (N.MaterialDesc * len(descs))(*[desc_struct(d) for d in descs])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(self.lib.bysdf_create_materials(arr, len(descs), _stream(stream), C.byref(h)),
+                    "bysdf_create_materials")
+        self.handle = h
+        self.n_mat = len(descs)
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.bysdf_destroy_materials(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, n: int) -> torch.Tensor:
+        need = int(self.lib.bysdf_workspace_size(self.handle, int(n)))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def set_params(self, params: torch.Tensor, stream=None):
+        p = params.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        assert p.shape == (self.n_mat, 8)
+        N.check(self.lib.bysdf_set_params(self.handle, _ptr(p), _stream(stream)), "bysdf_set_params")
+        self._params_keepalive = p
+
+    def get_params(self, stream=None) -> torch.Tensor:
+        p = torch.empty(self.n_mat, 8, dtype=torch.float32, device=self.device)
+        N.check(self.lib.bysdf_get_params(self.handle, _ptr(p), _stream(stream)), "bysdf_get_params")
+        return p
+
+    def set_launch_config(self, op: int, block: int, items: int, ctas_per_sm: int = 0):
+        c = N.LaunchConfig(block, items, ctas_per_sm, 0)
+        N.check(self.lib.bysdf_set_launch_config(self.handle, op, C.byref(c)), "set_launch_config")
+
+    def launch_config(self, op: int) -> dict:
+        c = N.LaunchConfig()
+        N.check(self.lib.bysdf_get_launch_config(self.handle, op, C.byref(c)), "get_launch_config")
+        return dict(block=c.block, items=c.items, ctas_per_sm=c.ctas_per_sm)
+
+    def workspace_error(self, stream=None) -> int:
+        err = C.c_uint32(0)
+        ws = self.workspace(0)
+        N.check(self.lib.bysdf_workspace_error(_ptr(ws), _stream(stream), C.byref(err)),
+                "bysdf_workspace_error")
+        return int(err.value)
+
+
+def hits_struct(rec: dict, sample: bool = False) -> N.Hits:
+    h = N.Hits()
+    h.h = _ptr(rec["h"])
+    h.u = _ptr(rec["u"])
+    h.v = _ptr(rec["v"])
+    h.wi = _ptr(rec["wi"])
+    h.wo = None if sample else _ptr(rec.get("wo"))
+    h.ratio = _ptr(rec.get("ratio"))
+    h.mat_id = _ptr(rec.get("mat_id"))
+    h.seg_offsets = _ptr(rec.get("seg_offsets"))
+    return h
+
+
+def records_to_device(rec: dict, device="cuda", seg_offsets=None) -> dict:
+    """numpy planes (see inputs.records) -> CUDA tensors."""
+    out = {}
+    for k, a in rec.items():
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        out[k] = t.to(device)
+    if seg_offsets is not None:
+        out["seg_offsets"] = torch.from_numpy(np.asarray(seg_offsets, np.int64)).to(device)
+    return out
+
+
+def _n(rec) -> int:
+    return int(rec["h"].shape[0])
+
+
+def _empty(shape, dtype, dev):
+    return torch.empty(shape, dtype=dtype, device=dev)
+
+
+def eval(mats: Materials, rec: dict, with_pdf: bool = True, stream=None, out=None):
+    """f |wo.n| (3, n), pdf (n,) and status (n,) uint8."""
+    n = _n(rec)
+    dev = rec["h"].device
+    f = out["f"] if out else _empty((3, n), torch.float32, dev)
+    pdf = (out["pdf"] if out else _empty((n,), torch.float32, dev)) if with_pdf else None
+    st = out["status"] if out else _empty((n,), torch.uint8, dev)
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval(mats.handle, C.byref(hits_struct(rec)), n, _ptr(f), _ptr(pdf),
+                                _ptr(st), _ptr(ws), ws.numel(), _stream(stream)), "bysdf_eval")
+    return f, pdf, st
+
+
+def sample(mats: Materials, rec: dict, u0=None, u1=None, stream=None, out=None):
+    """wo (3, n), weight (3, n), pdf (n,), lobe << 4 | status (n,)."""
+    n = _n(rec)
+    dev = rec["h"].device
+    u0 = rec["u0"] if u0 is None else u0
+    u1 = rec["u1"] if u1 is None else u1
+    if out:
+        wo, w, p, ls = out["wo"], out["weight"], out["pdf"], out["lobe_status"]
+    else:
+        wo, w = _empty((3, n), torch.float32, dev), _empty((3, n), torch.float32, dev)
+        p, ls = _empty((n,), torch.float32, dev), _empty((n,), torch.uint8, dev)
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_sample(mats.handle, C.byref(hits_struct(rec, sample=True)), _ptr(u0),
+                                  _ptr(u1), n, _ptr(wo), _ptr(w), _ptr(p), _ptr(ls), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "bysdf_sample")
+    return wo, w, p, ls
+
+
+def pdf(mats: Materials, rec: dict, stream=None, out=None):
+    n = _n(rec)
+    dev = rec["h"].device
+    p = out["pdf"] if out else _empty((n,), torch.float32, dev)
+    st = out["status"] if out else _empty((n,), torch.uint8, dev)
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_pdf(mats.handle, C.byref(hits_struct(rec)), n, _ptr(p), _ptr(st),
+                               _ptr(ws), ws.numel(), _stream(stream)), "bysdf_pdf")
+    return p, st
+
+
+def alloc_fused(n: int, dev) -> dict:
+    return dict(f=_empty((3, n), torch.float32, dev), pdf=_empty((n,), torch.float32, dev),
+                status=_empty((n,), torch.uint8, dev), wo=_empty((3, n), torch.float32, dev),
+                weight=_empty((3, n), torch.float32, dev), pdf_s=_empty((n,), torch.float32, dev),
+                lobe_status=_empty((n,), torch.uint8, dev))
+
+
+def eval_sample_pdf(mats: Materials, rec: dict, u0=None, u1=None, stream=None, out=None) -> dict:
+    """Fused eval + pdf at rec['wo'] and a sample from (u0, u1)."""
+    n = _n(rec)
+    o = out if out is not None else alloc_fused(n, rec["h"].device)
+    u0 = rec["u0"] if u0 is None else u0
+    u1 = rec["u1"] if u1 is None else u1
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_sample_pdf(
+        mats.handle, C.byref(hits_struct(rec)), _ptr(u0), _ptr(u1), n, _ptr(o["f"]),
+        _ptr(o["pdf"]), _ptr(o["status"]), _ptr(o["wo"]), _ptr(o["weight"]), _ptr(o["pdf_s"]),
+        _ptr(o["lobe_status"]), _ptr(ws), ws.numel(), _stream(stream)), "bysdf_eval_sample_pdf")
+    return o
+
+
+def eval_backward(mats: Materials, rec: dict, grad_f: torch.Tensor, deterministic: bool = False,
+                  stream=None, out=None) -> torch.Tensor:
+    """d(sum grad_f * f) / d params, shape (n_mat, 8)."""
+    n = _n(rec)
+    g = out if out is not None else _empty((mats.n_mat, 8), torch.float32, rec["h"].device)
+    gf = grad_f.contiguous()
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_backward(mats.handle, C.byref(hits_struct(rec)), n, _ptr(gf),
+                                         _ptr(g), int(deterministic), _ptr(ws), ws.numel(),
+                                         _stream(stream)), "bysdf_eval_backward")
+    return g
+
+
+def plain(op: int, mats: Materials, rec: dict, seg_host, stream=None, out=None) -> dict:
+    """The per-material-launch comparison form (records sorted by material)."""
+    n = _n(rec)
+    dev = rec["h"].device
+    seg = np.ascontiguousarray(seg_host, dtype=np.int64)
+    o = out if out is not None else dict(
+        f=_empty((3, n), torch.float32, dev), wo=_empty((3, n), torch.float32, dev),
+        weight=_empty((3, n), torch.float32, dev), pdf=_empty((n,), torch.float32, dev),
+        status=_empty((n,), torch.uint8, dev))
+    samp = op == N.OP_SAMPLE
+    N.check(mats.lib.bysdf_plain(
+        op, mats.handle, C.byref(hits_struct(rec, sample=samp)), seg.ctypes.data,
+        _ptr(rec.get("u0")) if samp else None, _ptr(rec.get("u1")) if samp else None, n,
+        _ptr(o["f"]), _ptr(o["wo"]), _ptr(o["weight"]), _ptr(o["pdf"]), _ptr(o["status"]),
+        _stream(stream)), "bysdf_plain")
+    return o
+
+
+def autotune(mats: Materials, op: int, rec: dict, out: dict | None = None, grad_f=None,
+             stream=None) -> dict:
+    n = _n(rec)
+    dev = rec["h"].device
+    o = out if out is not None else alloc_fused(n, dev)
+    gp = _empty((mats.n_mat, 8), torch.float32, dev)
+    outs = N.Outputs(_ptr(o["f"]), _ptr(o["pdf"]), _ptr(o["status"]), _ptr(o["wo"]),
+                     _ptr(o["weight"]), _ptr(o["pdf_s"]), _ptr(o["lobe_status"]), _ptr(gp))
+    ws = mats.workspace(n)
+    best = N.LaunchConfig()
+    samp = op == N.OP_SAMPLE
+    N.check(mats.lib.bysdf_autotune(
+        mats.handle, op, C.byref(hits_struct(rec, sample=samp)), _ptr(rec.get("u0")),
+        _ptr(rec.get("u1")), _ptr(grad_f), n, C.byref(outs), _ptr(ws), ws.numel(),
+        _stream(stream), C.byref(best)), "bysdf_autotune")
+    return dict(block=best.block, items=best.items, ctas_per_sm=best.ctas_per_sm)
+
+
+def default_params(descs) -> torch.Tensor:
+    """The 8 differentiable parameters of each descriptor (angles in radians)."""
+    d2r = np.pi / 180.0
+    rows = [[d["albedo"][0], d["albedo"][1], d["albedo"][2], d["beta_deg"][0] * d2r,
+             d["beta_deg"][1] * d2r, d["ply_twist_deg"] * d2r, d["fiber_twist_deg"] * d2r,
+             d["shadow_density"]] for d in descs]
+    return torch.tensor(np.asarray(rows, np.float64), dtype=torch.float32)
+
+
+class BYSDFEval(torch.autograd.Function):
+    """f = BYSDF(params; records), differentiable in the per-material
+    parameters; backward runs the library's recompute-and-reduce kernel."""
+
+    @staticmethod
+    def forward(ctx, params, mats, rec, deterministic=False):
+        mats.set_params(params)
+        f, _, st = eval(mats, rec, with_pdf=False)
+        ctx.mats, ctx.rec, ctx.det = mats, rec, deterministic
+        ctx.mark_non_differentiable(st)
+        return f, st
+
+    @staticmethod
+    def backward(ctx, grad_f, grad_st):
+        g = eval_backward(ctx.mats, ctx.rec, grad_f.float().contiguous(), ctx.det)
+        return g, None, None, None
+
+
+def bysdf(params: torch.Tensor, mats: Materials, rec: dict, deterministic: bool = False):
+    """Differentiable evaluation: returns f (3, n) and status (n,)."""
+    return BYSDFEval.apply(params, mats, rec, deterministic)
+
+
+# ------------------------------------------------------------ host buffers --
+_IN_KEYS = ("h", "u", "v", "wi", "wo", "u0", "u1", "mat_id")
+_OUT_KEYS = ("f", "pdf", "status", "wo", "weight", "pdf_s", "lobe_status")
+
+
+def pinned_records(rec: dict) -> dict:
+    """numpy planes -> pinned host tensors (for eval_sample_pdf_host)."""
+    return {k: torch.from_numpy(np.ascontiguousarray(rec[k])).pin_memory()
+            for k in _IN_KEYS if k in rec}
+
+
+def pinned_fused_outputs(n: int) -> dict:
+    o = alloc_fused(n, "cpu")
+    return {k: v.pin_memory() for k, v in o.items()}
+
+
+class HostPipeline:
+    """Eval + pdf + sample of records held in pinned HOST memory: each chunk
+    is copied to the device, run through the fused kernel and copied back,
+    with the copies of one chunk overlapping the kernel of the next (two
+    device slots; copy-in, compute and copy-out streams).  Slot buffers are
+    flat, so a chunk of m records is viewed as contiguous (3, m) planes."""
+
+    _IN_3 = ("wi", "wo")
+    _OUT_3 = ("f", "wo", "weight")
+
+    def __init__(self, mats: Materials, chunk: int, device="cuda"):
+        self.mats = mats
+        self.chunk = chunk
+        self.dev = torch.device(device)
+        self.s_in = torch.cuda.Stream(self.dev)
+        self.s_run = torch.cuda.Stream(self.dev)
+        self.s_out = torch.cuda.Stream(self.dev)
+        self.slots = []
+        for _ in range(2):
+            din = {k: _empty((3 * chunk if k in self._IN_3 else chunk,),
+                             torch.int32 if k == "mat_id" else torch.float32, self.dev)
+                   for k in _IN_KEYS}
+            dout = {k: _empty((3 * chunk if k in self._OUT_3 else chunk,),
+                              torch.uint8 if k in ("status", "lobe_status") else torch.float32,
+                              self.dev) for k in _OUT_KEYS}
+            self.slots.append((din, dout))
+        self.ws = [torch.empty(mats.lib.bysdf_workspace_size(mats.handle, chunk), dtype=torch.uint8,
+                               device=self.dev) for _ in range(2)]
+
+    def run(self, host_in: dict, host_out: dict):
+        n = int(host_in["h"].shape[0])
+        ev_free = [None, None]
+        main = torch.cuda.current_stream(self.dev)
+        self.s_in.wait_stream(main)
+        self.s_out.wait_stream(main)
+        for c, a in enumerate(range(0, n, self.chunk)):
+            b = min(n, a + self.chunk)
+            m = b - a
+            k = c & 1
+            din, dout = self.slots[k]
+            view_in = {key: (din[key][:3 * m].view(3, m) if key in self._IN_3 else din[key][:m])
+                       for key in _IN_KEYS if key in host_in}
+            view_out = {key: (dout[key][:3 * m].view(3, m) if key in self._OUT_3 else dout[key][:m])
+                        for key in _OUT_KEYS}
+            with torch.cuda.stream(self.s_in):
+                if ev_free[k] is not None:
+                    self.s_in.wait_event(ev_free[k])
+                for key, dst in view_in.items():
+                    src = host_in[key]
+                    if src.dim() == 2:
+                        for p in range(3):
+                            dst[p].copy_(src[p, a:b], non_blocking=True)
+                    else:
+                        dst.copy_(src[a:b], non_blocking=True)
+            e_in = torch.cuda.Event()
+            e_in.record(self.s_in)
+            self.s_run.wait_event(e_in)
+            ws = self.ws[k]
+            N.check(self.mats.lib.bysdf_eval_sample_pdf(
+                self.mats.handle, C.byref(hits_struct(view_in)), _ptr(view_in["u0"]),
+                _ptr(view_in["u1"]), m, _ptr(view_out["f"]), _ptr(view_out["pdf"]),
+                _ptr(view_out["status"]), _ptr(view_out["wo"]), _ptr(view_out["weight"]),
+                _ptr(view_out["pdf_s"]), _ptr(view_out["lobe_status"]), _ptr(ws), ws.numel(),
+                self.s_run.cuda_stream), "bysdf_eval_sample_pdf")
+            e_run = torch.cuda.Event()
+            e_run.record(self.s_run)
+            self.s_out.wait_event(e_run)
+            with torch.cuda.stream(self.s_out):
+                for key, src in view_out.items():
+                    if src.dim() == 2:
+                        for p in range(3):
+                            host_out[key][p, a:b].copy_(src[p], non_blocking=True)
+                    else:
+                        host_out[key][a:b].copy_(src, non_blocking=True)
+            ev_free[k] = torch.cuda.Event()
+            ev_free[k].record(self.s_out)
+        main.wait_stream(self.s_out)
+
+    @staticmethod
+    def bytes_per_record(host_in: dict, host_out: dict):
+        n = int(host_in["h"].shape[0])
+        bi = sum(t.numel() * t.element_size() for t in host_in.values()) / n
+        bo = sum(t.numel() * t.element_size() for t in host_out.values()) / n
+        return bi, bo

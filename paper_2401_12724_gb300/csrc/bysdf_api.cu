@@ -1,0 +1,724 @@
+// Host side of libbysdf: the C ABI of include/bysdf.h.  Descriptor
+// validation, the material table builder (layout, derived constants and the
+// 1D fiber maps, computed in double on the host), workspace planning, kernel
+// dispatch, the plain per-material form and the launch-shape autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "bysdf.h"
+#include "bysdf_launch.h"
+
+using namespace bysdf;
+
+struct bysdf_materials {
+  int device = 0;
+  int n_mat = 0;
+  int t_max = 0;
+  int stride = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  uint8_t* d_table = nullptr;
+  std::vector<bysdf_material_desc> desc;
+  bysdf_launch_config cfg[BYSDF_NOPS];
+};
+
+namespace {
+
+constexpr double kPiD = 3.14159265358979323846;
+// Tables up to this size are staged whole into each CTA's shared memory.
+constexpr size_t kAllSmemMax = 48 * 1024;
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define BY_CU(x)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(BYSDF_E_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ------------------------------------------------------------- layout ----
+// Reading of Sec. 3.4 / 3.5 (the paper gives no layout): N_p equal ply discs
+// inscribed in the yarn circle and touching their neighbours; N_f fibers of
+// one radius filling `packing` of a ply disc; the outer ring holds the fewest
+// fibers whose circles close it.
+struct HostLayout {
+  double R, Rp, Rc, rf, Rfc;
+  int M;
+};
+
+bool host_layout(const bysdf_material_desc& d, HostLayout* L, std::string* why) {
+  auto bad = [&](const char* s) {
+    *why = s;
+    return false;
+  };
+  auto fin = [](double x) { return std::isfinite(x); };
+  if (d.n_plies < 1 || d.n_plies > kMaxPlies) return bad("n_plies outside [1, 8]");
+  if (d.fibers_per_ply < 4 || d.fibers_per_ply > 4096) return bad("fibers_per_ply outside [4, 4096]");
+  if (d.map_texels < 4 || d.map_texels > kMaxTexels) return bad("map_texels outside [4, 1024]");
+  if (d.trace_iters < 1 || d.trace_iters > 64) return bad("trace_iters outside [1, 64]");
+  if (d.k_max < 1 || d.k_max > 64) return bad("k_max outside [1, 64]");
+  if (!(d.yarn_radius > 0.f) || !fin(d.yarn_radius)) return bad("yarn_radius must be > 0");
+  if (!(d.eta > 1.f) || !fin(d.eta)) return bad("eta must be > 1");
+  if (!(d.packing > 0.f && d.packing <= 1.f)) return bad("packing outside (0, 1]");
+  if (!(d.body_B >= 0.f && d.body_B <= 1.f)) return bad("body_B outside [0, 1]");
+  if (!(d.body_r >= 0.f && d.body_r <= 1.f)) return bad("body_r outside [0, 1]");
+  if (!(d.k_spec >= 0.f) || !fin(d.k_spec)) return bad("k_spec must be >= 0");
+  if (!(d.sigma_t >= 0.f) || !fin(d.sigma_t)) return bad("sigma_t must be >= 0");
+  if (!(d.shadow_density >= 0.f) || !fin(d.shadow_density)) return bad("shadow_density must be >= 0");
+  for (int c = 0; c < 3; ++c)
+    if (!fin(d.albedo[c])) return bad("albedo must be finite");
+  for (int c = 0; c < 2; ++c)
+    if (!fin(d.beta_deg[c])) return bad("beta_deg must be finite");
+  if (!fin(d.ply_twist_deg) || std::fabs(d.ply_twist_deg) >= 89.f) return bad("ply_twist_deg outside (-89, 89)");
+  if (!fin(d.fiber_twist_deg) || std::fabs(d.fiber_twist_deg) >= 89.f)
+    return bad("fiber_twist_deg outside (-89, 89)");
+  L->R = d.yarn_radius;
+  if (d.n_plies == 1) {
+    L->Rp = L->R;
+    L->Rc = 0.0;
+  } else {
+    const double s = std::sin(kPiD / d.n_plies);
+    L->Rc = L->R / (1.0 + s);
+    L->Rp = L->Rc * s;
+  }
+  L->rf = L->Rp * std::sqrt((double)d.packing / (double)d.fibers_per_ply);
+  L->Rfc = L->Rp - L->rf;
+  if (!(L->rf < L->Rfc)) return bad("fibers too thick for the ply (raise fibers_per_ply)");
+  L->M = (int)std::ceil(kPiD / std::asin(L->rf / L->Rfc));
+  return true;
+}
+
+// ------------------------------------------------------------ fiber maps --
+// Sec. 3.5.1: along the radial line at angular offset D from a fiber centre
+// the outer fiber surface has normal tilted by delta from the radial
+// direction.  Sec. 4.1.4: o_f is the share of the outward half-plane of
+// directions at that point hidden by the other fibers of the ring.
+double map_delta(const HostLayout& L, double D) {
+  const double sd = L.Rfc * std::sin(D);
+  return std::atan2(sd, std::sqrt(std::max(0.0, L.rf * L.rf - sd * sd)));
+}
+
+double map_occlusion(const HostLayout& L, double D) {
+  const double sd = L.Rfc * std::sin(D);
+  const double rho = L.Rfc * std::cos(D) + std::sqrt(std::max(0.0, L.rf * L.rf - sd * sd));
+  const double px = rho * std::cos(D), py = rho * std::sin(D);
+  const double normal_angle = std::atan2(py, px - L.Rfc);
+  // sweep over interval end points ("events") inside [-pi/2, pi/2]
+  std::vector<std::pair<double, int>> ev;
+  for (int j = 1; j < L.M; ++j) {
+    const double cj = 2.0 * kPiD * j / L.M;
+    const double dx = L.Rfc * std::cos(cj) - px, dy = L.Rfc * std::sin(cj) - py;
+    const double dist = std::hypot(dx, dy);
+    const double half = dist > L.rf ? std::asin(L.rf / dist) : 0.5 * kPiD;
+    double mid = std::remainder(std::atan2(dy, dx) - normal_angle, 2.0 * kPiD);
+    for (double shift : {-2.0 * kPiD, 0.0, 2.0 * kPiD}) {
+      const double a = std::max(mid + shift - half, -0.5 * kPiD);
+      const double b = std::min(mid + shift + half, 0.5 * kPiD);
+      if (b > a) {
+        ev.push_back({a, +1});
+        ev.push_back({b, -1});
+      }
+    }
+  }
+  std::sort(ev.begin(), ev.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+    return x.first < y.first || (x.first == y.first && x.second > y.second);
+  });
+  double covered = 0.0, start = 0.0;
+  int depth = 0;
+  for (const auto& e : ev) {
+    if (depth == 0 && e.second > 0) start = e.first;
+    depth += e.second;
+    if (depth == 0 && e.second < 0) covered += e.first - start;
+  }
+  return covered / kPiD;
+}
+
+// Derived constants from the 8 parameters (radians), shared by table
+// creation on the host and parameter updates on the device.
+__host__ __device__ void split_hi_lo(double x, float* hi, float* lo) {
+  *hi = (float)x;
+  *lo = (float)(x - (double)*hi);
+}
+
+__host__ __device__ void derive_constants(MatDev& m, const double* p) {
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  m.alb[0] = (float)p[0];
+  m.alb[1] = (float)p[1];
+  m.alb[2] = (float)p[2];
+  m.beta_t = (float)p[3];
+  m.beta_b = (float)p[4];
+  m.alpha_p = (float)p[5];
+  m.alpha_f = (float)p[6];
+  m.sigma_s = (float)p[7];
+  if (m.np == 1) {
+    m.kp_hi = m.kp_lo = 0.f;
+    m.dkp = 0.f;
+  } else {
+    const double t = tan(p[5]);
+    split_hi_lo(t / (two_pi * m.Rc_d), &m.kp_hi, &m.kp_lo);
+    m.dkp = (float)((1.0 + t * t) / (two_pi * m.Rc_d));
+  }
+  const double tf = tan(p[6]);
+  split_hi_lo(tf * m.M / (two_pi * m.Rfc_d), &m.kf_hi, &m.kf_lo);
+  m.dkf = (float)((1.0 + tf * tf) * m.M / (two_pi * m.Rfc_d));
+  m.cos_af = (float)cos(p[6]);
+  m.sin_af = (float)sin(p[6]);
+}
+
+__global__ void k_update_params(uint8_t* table, int n_mat, int stride, const float* params) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_mat) return;
+  MatDev* m = reinterpret_cast<MatDev*>(table + (size_t)i * stride);
+  double p[8];
+  for (int k = 0; k < 8; ++k) p[k] = (double)params[i * 8 + k];
+  derive_constants(*m, p);
+}
+
+__global__ void k_read_params(const uint8_t* table, int n_mat, int stride, float* params) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_mat) return;
+  const MatDev* m = reinterpret_cast<const MatDev*>(table + (size_t)i * stride);
+  const float p[8] = {m->alb[0], m->alb[1], m->alb[2], m->beta_t,
+                      m->beta_b, m->alpha_p, m->alpha_f, m->sigma_s};
+  for (int k = 0; k < 8; ++k) params[i * 8 + k] = p[k];
+}
+
+// Tile plan: reset the tile counter; for material-sorted records also the
+// first warp tile of every material (exclusive scan of ceil(count / tile)).
+__global__ void __launch_bounds__(1024) k_plan(WsCtl* ctl, int32_t* tile_start,
+                                               const int64_t* seg, int n_mat, int tile) {
+  __shared__ int64_t part[1024];
+  const int tid = threadIdx.x;
+  if (seg != nullptr) {
+    const int chunk = (n_mat + 1023) / 1024;
+    const int b = min(tid * chunk, n_mat), e = min(b + chunk, n_mat);
+    int64_t s = 0;
+    for (int m = b; m < e; ++m) {
+      const int64_t c = seg[m + 1] - seg[m];
+      s += c > 0 ? (c + tile - 1) / tile : 0;
+    }
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int64_t v = tid >= off ? part[tid - off] : 0;
+      __syncthreads();
+      part[tid] += v;
+      __syncthreads();
+    }
+    int64_t run = part[tid] - s;  // exclusive prefix
+    for (int m = b; m < e; ++m) {
+      tile_start[m] = (int32_t)run;
+      const int64_t c = seg[m + 1] - seg[m];
+      run += c > 0 ? (c + tile - 1) / tile : 0;
+    }
+    if (tid == 1023) tile_start[n_mat] = (int32_t)part[1023];
+  }
+  if (tid == 0) ctl->tile_counter = 0;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+size_t ws_tile_start_off() { return kWsCtl; }
+size_t ws_partials_off(int n_mat) { return align_up(kWsCtl + 4 * (size_t)(n_mat + 1), 256); }
+int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
+
+bysdf_launch_config default_cfg() {
+  bysdf_launch_config c;
+  c.block = 256;
+  c.items = 2;
+  c.ctas_per_sm = 0;  // 0: as many as fit
+  c.reserved = 0;
+  return c;
+}
+
+int check_hits(const bysdf_materials* m, const bysdf_hits* h, bool need_wo, int64_t n) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  if (!h) return fail(BYSDF_E_ARG, "hits is NULL");
+  if (n < 0) return fail(BYSDF_E_ARG, "n < 0");
+  if (n == 0) return BYSDF_OK;
+  if (n > ((int64_t)1 << 36)) return fail(BYSDF_E_ARG, "n too large");
+  if (!h->h || !h->u || !h->v || !h->wi) return fail(BYSDF_E_ARG, "hits: h, u, v, wi required");
+  if (need_wo && !h->wo) return fail(BYSDF_E_ARG, "hits: wo required");
+  const void* ps[] = {h->h, h->u, h->v, h->wi, need_wo ? h->wo : nullptr, h->ratio, h->mat_id,
+                      h->seg_offsets};
+  for (const void* p : ps)
+    if (p && !aligned16(p)) return fail(BYSDF_E_ARG, "hits: buffer not 16-byte aligned");
+  return BYSDF_OK;
+}
+
+int check_out(const void* p, const char* name) {
+  if (!p) return fail(BYSDF_E_ARG, std::string(name) + " is NULL");
+  if (!aligned16(p)) return fail(BYSDF_E_ARG, std::string(name) + " not 16-byte aligned");
+  return BYSDF_OK;
+}
+
+// Common preparation of a persistent launch.
+int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, size_t ws_bytes,
+            int block, int items, KArgs* a) {
+  std::memset(a, 0, sizeof(*a));
+  a->table = m->d_table;
+  a->n_mat = m->n_mat;
+  a->stride = m->stride;
+  a->n = n;
+  a->tile = 32 * items;
+  a->h = h->h;
+  a->u = h->u;
+  a->v = h->v;
+  a->wi = h->wi;
+  a->wo = h->wo;
+  a->ratio = h->ratio;
+  a->mat_id = h->mat_id;
+  a->seg = h->seg_offsets;
+  if (h->seg_offsets) {
+    a->mode = MODE_SORTED;
+  } else if ((size_t)m->n_mat * m->stride <= kAllSmemMax) {
+    a->mode = MODE_ALL_SMEM;
+  } else {
+    return fail(BYSDF_E_UNSUPPORTED,
+                "tables do not fit in shared memory: pass material-sorted records with seg_offsets");
+  }
+  a->n_tiles = (n + a->tile - 1) / a->tile;
+  if (!ws) return fail(BYSDF_E_WORKSPACE, "workspace is NULL");
+  if (!aligned16(ws)) return fail(BYSDF_E_ARG, "workspace not 16-byte aligned");
+  if (ws_bytes < bysdf_workspace_size(m, n))
+    return fail(BYSDF_E_WORKSPACE, "workspace smaller than bysdf_workspace_size()");
+  a->ctl = reinterpret_cast<WsCtl*>(ws);
+  a->tile_start = reinterpret_cast<const int32_t*>((uint8_t*)ws + ws_tile_start_off());
+  (void)block;
+  return BYSDF_OK;
+}
+
+int plan(const bysdf_materials* m, KArgs& a, void* ws, cudaStream_t st) {
+  k_plan<<<1, 1024, 0, st>>>(a.ctl, reinterpret_cast<int32_t*>((uint8_t*)ws + ws_tile_start_off()),
+                             a.mode == MODE_SORTED ? a.seg : nullptr, m->n_mat, a.tile);
+  BY_CU(cudaGetLastError());
+  return BYSDF_OK;
+}
+
+int grid_for(const bysdf_materials* m, const bysdf_launch_config& c, int occ) {
+  int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+  return m->sm_count * per_sm;
+}
+
+int op_bits(int op) {
+  switch (op) {
+    case BYSDF_OP_EVAL: return OPF_EVAL;
+    case BYSDF_OP_SAMPLE: return OPF_SAMPLE;
+    case BYSDF_OP_PDF: return OPF_PDF;
+    case BYSDF_OP_FUSED: return OPF_EVAL | OPF_SAMPLE;
+  }
+  return 0;
+}
+
+int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const float* u0,
+                const float* u1, int64_t n, const bysdf_outputs& o, void* ws, size_t ws_bytes,
+                cudaStream_t st, const bysdf_launch_config& c) {
+  const int bits = op_bits(op);
+  const bool need_wo = (bits & (OPF_EVAL | OPF_PDF)) != 0;
+  int rc = check_hits(m, h, need_wo, n);
+  if (rc) return rc;
+  if (bits & OPF_EVAL) {
+    if ((rc = check_out(o.f_rgb, "f_rgb"))) return rc;
+  }
+  if (bits & (OPF_EVAL | OPF_PDF)) {
+    if ((rc = check_out(o.status, "status"))) return rc;
+    if ((bits & OPF_PDF) && (rc = check_out(o.pdf, "pdf"))) return rc;
+    if (o.pdf && !aligned16(o.pdf)) return fail(BYSDF_E_ARG, "pdf not 16-byte aligned");
+  }
+  if (bits & OPF_SAMPLE) {
+    if ((rc = check_out(u0, "u0")) || (rc = check_out(u1, "u1"))) return rc;
+    if ((rc = check_out(o.wo, "wo")) || (rc = check_out(o.weight, "weight")) ||
+        (rc = check_out(o.pdf_s, "pdf (sample)")) || (rc = check_out(o.lobe_status, "lobe_status")))
+      return rc;
+  }
+  if (n == 0) return BYSDF_OK;
+  KArgs a;
+  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a))) return rc;
+  if (!(bits & OPF_SAMPLE) || bits == (OPF_EVAL | OPF_SAMPLE)) a.wo = h->wo;
+  if (bits == OPF_SAMPLE) a.wo = nullptr;
+  a.u0 = u0;
+  a.u1 = u1;
+  a.f_rgb = o.f_rgb;
+  a.pdf = o.pdf;
+  a.status = o.status;
+  a.wo_s = o.wo;
+  a.weight_s = o.weight;
+  a.pdf_s = o.pdf_s;
+  a.lstat_s = o.lobe_status;
+  const size_t smem = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
+                                              : (size_t)(c.block / 32) * m->stride;
+  if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
+  if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, smem));
+  int occ = 0;
+  BY_CU(forward_occupancy(bits, c.block, smem, &occ));
+  if ((rc = plan(m, a, ws, st))) return rc;
+  BY_CU(launch_forward(bits, a, c.block, grid_for(m, c, occ), smem, st));
+  return BYSDF_OK;
+}
+
+int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const float* grad_f,
+                 float* grad_params, int deterministic, void* ws, size_t ws_bytes,
+                 cudaStream_t st, const bysdf_launch_config& c) {
+  int rc = check_hits(m, h, true, n);
+  if (rc) return rc;
+  if ((rc = check_out(grad_params, "grad_params"))) return rc;
+  if (n > 0 && (rc = check_out(grad_f, "grad_f"))) return rc;
+  if (deterministic && !h->seg_offsets)
+    return fail(BYSDF_E_UNSUPPORTED, "deterministic backward needs material-sorted records");
+  if (n == 0) {
+    BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * 8 * m->n_mat, st));
+    return BYSDF_OK;
+  }
+  KArgs a;
+  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a))) return rc;
+  a.grad_f = grad_f;
+  a.grad_params = grad_params;
+  a.partials = deterministic ? reinterpret_cast<float*>((uint8_t*)ws + ws_partials_off(m->n_mat))
+                             : nullptr;
+  const size_t smem = a.mode == MODE_ALL_SMEM
+                          ? (size_t)m->n_mat * m->stride + sizeof(float) * 8 * m->n_mat
+                          : (size_t)(c.block / 32) * m->stride;
+  if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
+  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, smem));
+  int occ = 0;
+  BY_CU(backward_occupancy(c.block, smem, &occ));
+  if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * 8 * m->n_mat, st));
+  if ((rc = plan(m, a, ws, st))) return rc;
+  BY_CU(launch_backward(a, c.block, grid_for(m, c, occ), smem, st));
+  if (deterministic) BY_CU(launch_reduce_partials(a, st));
+  return BYSDF_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI ==
+extern "C" {
+
+const char* bysdf_version(void) { return "libbysdf 0.1 (sm_103a)"; }
+
+const char* bysdf_last_error(void) { return g_err.c_str(); }
+
+int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* stream,
+                           bysdf_materials** out) {
+  if (!desc || !out) return fail(BYSDF_E_ARG, "desc and out must not be NULL");
+  if (n < 1 || n > 65536) return fail(BYSDF_E_ARG, "n outside [1, 65536]");
+  *out = nullptr;
+  std::vector<HostLayout> L(n);
+  int t_max = 0;
+  for (int i = 0; i < n; ++i) {
+    std::string why;
+    if (!host_layout(desc[i], &L[i], &why))
+      return fail(BYSDF_E_ARG, "material " + std::to_string(i) + ": " + why);
+    t_max = std::max(t_max, desc[i].map_texels);
+  }
+  const size_t stride = mat_stride_bytes(t_max);
+  std::vector<uint8_t> host(stride * n, 0);
+  for (int i = 0; i < n; ++i) {
+    const bysdf_material_desc& d = desc[i];
+    MatDev& m = *reinterpret_cast<MatDev*>(host.data() + stride * i);
+    m.np = d.n_plies;
+    m.M = L[i].M;
+    m.T = d.map_texels;
+    m.nit = d.trace_iters;
+    m.kmax = d.k_max;
+    m.flags = d.flags;
+    m.R = (float)L[i].R;
+    m.Rp = (float)L[i].Rp;
+    m.Rc = (float)L[i].Rc;
+    m.Rfc = (float)L[i].Rfc;
+    m.Rc_d = L[i].Rc;
+    m.Rfc_d = L[i].Rfc;
+    m.eta = d.eta;
+    m.inv_eta = (float)(1.0 / (double)d.eta);
+    m.B = d.body_B;
+    m.r = d.body_r;
+    m.ks = (float)((1.0 - (double)d.body_B) * (double)d.k_spec);
+    m.sigma_t = d.sigma_t;
+    m.inv_2Rp = (float)(0.5 / L[i].Rp);
+    m.m_over_2pi = (float)(L[i].M / (2.0 * kPiD));
+    m.inv_np = (float)(1.0 / d.n_plies);
+    for (int j = 0; j < kMaxPlies; ++j) {
+      m.rot_c[j] = (float)std::cos(2.0 * kPiD * j / d.n_plies);
+      m.rot_s[j] = (float)std::sin(2.0 * kPiD * j / d.n_plies);
+    }
+    const double deg = kPiD / 180.0;
+    const double p[8] = {d.albedo[0], d.albedo[1], d.albedo[2], d.beta_deg[0] * deg,
+                         d.beta_deg[1] * deg, d.ply_twist_deg * deg, d.fiber_twist_deg * deg,
+                         d.shadow_density};
+    derive_constants(m, p);
+    float2* map = reinterpret_cast<float2*>(&m + 1);
+    for (int t = 0; t < d.map_texels; ++t) {
+      if (d.flags & 1) {
+        map[t] = make_float2(0.f, 0.f);
+        continue;
+      }
+      const double D = ((t + 0.5) / d.map_texels - 0.5) * 2.0 * kPiD / L[i].M;
+      map[t] = make_float2((float)map_delta(L[i], D), (float)map_occlusion(L[i], D));
+    }
+  }
+  bysdf_materials* M = new bysdf_materials();
+  M->n_mat = n;
+  M->t_max = t_max;
+  M->stride = (int)stride;
+  M->desc.assign(desc, desc + n);
+  for (int k = 0; k < BYSDF_NOPS; ++k) M->cfg[k] = default_cfg();
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  auto cleanup = [&](int rc) {
+    if (M->d_table) cudaFree(M->d_table);
+    delete M;
+    return rc;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&M->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&M->sm_count, cudaDevAttrMultiProcessorCount, M->device)) !=
+          cudaSuccess)
+    return cleanup(fail(BYSDF_E_CUDA, std::string("device query: ") + cudaGetErrorString(e)));
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, M->device);
+  M->smem_optin = (size_t)optin;
+  if ((e = cudaMalloc(&M->d_table, host.size())) != cudaSuccess)
+    return cleanup(fail(BYSDF_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
+  if ((e = cudaMemcpyAsync(M->d_table, host.data(), host.size(), cudaMemcpyHostToDevice, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cleanup(fail(BYSDF_E_CUDA, std::string("table upload: ") + cudaGetErrorString(e)));
+  *out = M;
+  return BYSDF_OK;
+}
+
+int bysdf_destroy_materials(bysdf_materials* m) {
+  if (!m) return BYSDF_OK;
+  cudaDeviceSynchronize();
+  if (m->d_table) cudaFree(m->d_table);
+  delete m;
+  return BYSDF_OK;
+}
+
+int32_t bysdf_num_materials(const bysdf_materials* m) { return m ? m->n_mat : 0; }
+
+int bysdf_set_params(bysdf_materials* m, const float* params, void* stream) {
+  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_update_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride, params);
+  BY_CU(cudaGetLastError());
+  return BYSDF_OK;
+}
+
+int bysdf_get_params(const bysdf_materials* m, float* params, void* stream) {
+  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_read_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride, params);
+  BY_CU(cudaGetLastError());
+  return BYSDF_OK;
+}
+
+size_t bysdf_workspace_size(const bysdf_materials* m, int64_t n) {
+  if (!m) return 0;
+  return ws_partials_off(m->n_mat) + sizeof(float) * 8 * (size_t)max_tiles(n, m->n_mat);
+}
+
+int bysdf_eval(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* f_rgb,
+               float* pdf, uint8_t* status, void* workspace, size_t workspace_bytes,
+               void* stream) {
+  bysdf_outputs o{};
+  o.f_rgb = f_rgb;
+  o.pdf = pdf;
+  o.status = status;
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_EVAL]);
+}
+
+int bysdf_sample(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,
+                 const float* u1, int64_t n, float* wo, float* weight, float* pdf,
+                 uint8_t* lobe_status, void* workspace, size_t workspace_bytes, void* stream) {
+  bysdf_outputs o{};
+  o.wo = wo;
+  o.weight = weight;
+  o.pdf_s = pdf;
+  o.lobe_status = lobe_status;
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_forward(m, BYSDF_OP_SAMPLE, hits, u0, u1, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_SAMPLE]);
+}
+
+int bysdf_pdf(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* pdf,
+              uint8_t* status, void* workspace, size_t workspace_bytes, void* stream) {
+  bysdf_outputs o{};
+  o.pdf = pdf;
+  o.status = status;
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_forward(m, BYSDF_OP_PDF, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_PDF]);
+}
+
+int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,
+                          const float* u1, int64_t n, float* f_rgb, float* pdf,
+                          uint8_t* status, float* wo_s, float* weight_s, float* pdf_s,
+                          uint8_t* lobe_status_s, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  bysdf_outputs o{};
+  o.f_rgb = f_rgb;
+  o.pdf = pdf;
+  o.status = status;
+  o.wo = wo_s;
+  o.weight = weight_s;
+  o.pdf_s = pdf_s;
+  o.lobe_status = lobe_status_s;
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_forward(m, BYSDF_OP_FUSED, hits, u0, u1, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED]);
+}
+
+int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                        const float* grad_f, float* grad_params, int deterministic,
+                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_backward(m, hits, n, grad_f, grad_params, deterministic, workspace,
+                      workspace_bytes, reinterpret_cast<cudaStream_t>(stream),
+                      m->cfg[BYSDF_OP_BACKWARD]);
+}
+
+int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
+                const int64_t* seg_offsets_host, const float* u0, const float* u1, int64_t n,
+                float* f_rgb, float* wo, float* weight, float* pdf, uint8_t* status,
+                void* stream) {
+  const int bits = op_bits(op);
+  if (bits != OPF_EVAL && bits != OPF_SAMPLE && bits != OPF_PDF)
+    return fail(BYSDF_E_ARG, "bysdf_plain: op must be EVAL, SAMPLE or PDF");
+  int rc = check_hits(m, hits, bits != OPF_SAMPLE, n);
+  if (rc) return rc;
+  if (!seg_offsets_host) return fail(BYSDF_E_ARG, "seg_offsets_host is NULL");
+  if (seg_offsets_host[0] != 0 || seg_offsets_host[m->n_mat] != n)
+    return fail(BYSDF_E_ARG, "seg_offsets_host must run from 0 to n");
+  for (int i = 0; i < m->n_mat; ++i)
+    if (seg_offsets_host[i + 1] < seg_offsets_host[i])
+      return fail(BYSDF_E_ARG, "seg_offsets_host must be non-decreasing");
+  if ((rc = check_out(status, "status"))) return rc;
+  if (bits == OPF_EVAL && (rc = check_out(f_rgb, "f_rgb"))) return rc;
+  if (bits != OPF_EVAL && (rc = check_out(pdf, "pdf"))) return rc;
+  if (bits == OPF_SAMPLE) {
+    if ((rc = check_out(u0, "u0")) || (rc = check_out(u1, "u1")) || (rc = check_out(wo, "wo")) ||
+        (rc = check_out(weight, "weight")))
+      return rc;
+  }
+  if (n == 0) return BYSDF_OK;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.table = m->d_table;
+  a.n_mat = m->n_mat;
+  a.stride = m->stride;
+  a.n = n;
+  a.h = hits->h;
+  a.u = hits->u;
+  a.v = hits->v;
+  a.wi = hits->wi;
+  a.wo = bits == OPF_SAMPLE ? nullptr : hits->wo;
+  a.ratio = hits->ratio;
+  a.u0 = u0;
+  a.u1 = u1;
+  a.f_rgb = f_rgb;
+  a.pdf = pdf;
+  a.status = status;
+  a.wo_s = wo;
+  a.weight_s = weight;
+  a.pdf_s = pdf;
+  a.lstat_s = status;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < m->n_mat; ++i)
+    BY_CU(launch_plain(bits, a, i, seg_offsets_host[i], seg_offsets_host[i + 1], st));
+  return BYSDF_OK;
+}
+
+int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_config* cfg) {
+  if (!m || !cfg) return fail(BYSDF_E_ARG, "NULL argument");
+  if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
+  if (cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
+    return fail(BYSDF_E_ARG, "block must be 128, 256 or 512");
+  if (cfg->items < 1 || cfg->items > 8) return fail(BYSDF_E_ARG, "items outside [1, 8]");
+  if (cfg->ctas_per_sm < 0) return fail(BYSDF_E_ARG, "ctas_per_sm < 0");
+  m->cfg[op] = *cfg;
+  return BYSDF_OK;
+}
+
+int bysdf_get_launch_config(const bysdf_materials* m, int op, bysdf_launch_config* cfg) {
+  if (!m || !cfg) return fail(BYSDF_E_ARG, "NULL argument");
+  if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
+  *cfg = m->cfg[op];
+  return BYSDF_OK;
+}
+
+int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const float* u0,
+                   const float* u1, const float* grad_f, int64_t n, const bysdf_outputs* out,
+                   void* workspace, size_t workspace_bytes, void* stream,
+                   bysdf_launch_config* best) {
+  if (!m || !out || !best) return fail(BYSDF_E_ARG, "NULL argument");
+  if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  BY_CU(cudaEventCreate(&e0));
+  BY_CU(cudaEventCreate(&e1));
+  auto run = [&](const bysdf_launch_config& c) {
+    if (op == BYSDF_OP_BACKWARD)
+      return run_backward(m, hits, n, grad_f, out->grad_params, 0, workspace, workspace_bytes,
+                          st, c);
+    return run_forward(m, op, hits, u0, u1, n, *out, workspace, workspace_bytes, st, c);
+  };
+  float best_ms = 1e30f;
+  bysdf_launch_config best_c = m->cfg[op];
+  int rc = BYSDF_OK;
+  for (int block : {128, 256, 512}) {
+    for (int items : {1, 2, 4}) {
+      for (int cps : {0, 1, 2}) {
+        bysdf_launch_config c{block, items, cps, 0};
+        if ((rc = run(c))) break;  // warm-up (and validation)
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && rc == BYSDF_OK; ++r) rc = run(c);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = fail(BYSDF_E_CUDA, "autotune: kernel failed");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_c = c;
+        }
+      }
+      if (rc) break;
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  m->cfg[op] = best_c;
+  *best = best_c;
+  return BYSDF_OK;
+}
+
+int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err) {
+  if (!workspace || !err) return fail(BYSDF_E_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(workspace) + offsetof(WsCtl, err);
+  BY_CU(cudaMemcpyAsync(err, p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  BY_CU(cudaStreamSynchronize(st));
+  BY_CU(cudaMemsetAsync(const_cast<uint8_t*>(p), 0, sizeof(uint32_t), st));
+  return BYSDF_OK;
+}
+
+}  // extern "C"

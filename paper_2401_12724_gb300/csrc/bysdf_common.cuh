@@ -1,0 +1,223 @@
+// Shared device definitions of libbysdf: the per-material table layout, a
+// forward-mode dual number for the backward kernels, and small vector math.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bysdf {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr int kMaxPlies = 8;
+constexpr int kMaxTexels = 1024;
+
+// Per-material constants, 256 bytes, followed in memory by `T` float2 texels
+// (delta, o_f) of the 1D fiber maps (Sec. 3.5.1: fiber normal tilt delta;
+// Sec. 4.1.4: fiber self-occlusion o_f), one fiber period at texel centres.
+struct alignas(16) MatDev {
+  int32_t np, M, T, nit;      // plies, outer-ring fibers, texels, trace updates
+  int32_t kmax, flags, pad0, pad1;
+  float R, Rp, Rc, Rfc;       // yarn / ply radius, ply-centre radius, fiber ring radius
+  float eta, inv_eta, B, r;   // refractive index, body share, body reflect share
+  float ks, sigma_t, sigma_s, inv_2Rp;  // (1 - B) k_spec, extinction, shadow density
+  float alb[3], m_over_2pi;   // body albedo, M / (2 pi)
+  float beta_t, beta_b, alpha_p, alpha_f;  // differentiable angles (radians)
+  float kp_hi, kp_lo;         // ply helix rate in turns per length, split hi + lo
+  float kf_hi, kf_lo;         // fiber phase rate in map periods per length, split
+  float cos_af, sin_af;       // fiber helix angle
+  float dkp, dkf;             // d kp / d alpha_p, d kf / d alpha_f
+  float inv_np, pad2, pad3, pad4;
+  float rot_c[kMaxPlies], rot_s[kMaxPlies];  // cos, sin of 2 pi j / N_p
+  double Rc_d, Rfc_d;         // layout radii in double (derived-constant updates)
+  float pad5[4];
+};
+static_assert(sizeof(MatDev) == 256, "MatDev must be 256 bytes");
+
+__host__ __device__ inline size_t mat_stride_bytes(int t_max) {
+  return sizeof(MatDev) + sizeof(float2) * (size_t)t_max;
+}
+
+// Differentiable parameter slots carried by the dual numbers of the backward
+// kernels (albedo is linear and handled in closed form).
+enum { D_BETA_T = 0, D_BETA_B = 1, D_ALPHA_P = 2, D_ALPHA_F = 3, D_SIGMA_S = 4, ND = 5 };
+
+// ------------------------------------------------------------ dual numbers --
+template <int N>
+struct DualF {
+  float v;
+  float d[N];
+  DualF() = default;
+  __device__ __forceinline__ DualF(float x) : v(x) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) d[k] = 0.f;
+  }
+};
+
+template <class S> struct is_dual { static constexpr bool value = false; };
+template <int N> struct is_dual<DualF<N>> { static constexpr bool value = true; };
+
+__device__ __forceinline__ float vf(float x) { return x; }
+template <int N> __device__ __forceinline__ float vf(const DualF<N>& x) { return x.v; }
+
+#define BY_DF template <int N> __device__ __forceinline__ DualF<N>
+BY_DF operator+(const DualF<N>& a, const DualF<N>& b) {
+  DualF<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+BY_DF operator-(const DualF<N>& a, const DualF<N>& b) {
+  DualF<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+BY_DF operator-(const DualF<N>& a) {
+  DualF<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+BY_DF operator*(const DualF<N>& a, const DualF<N>& b) {
+  DualF<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = fmaf(a.d[k], b.v, a.v * b.d[k]);
+  return r;
+}
+BY_DF operator/(const DualF<N>& a, const DualF<N>& b) {
+  DualF<N> r;
+  const float inv = 1.0f / b.v;
+  r.v = a.v * inv;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * inv;
+  return r;
+}
+BY_DF operator+(const DualF<N>& a, float b) {
+  DualF<N> r = a;
+  r.v += b;
+  return r;
+}
+BY_DF operator+(float a, const DualF<N>& b) { return b + a; }
+BY_DF operator-(const DualF<N>& a, float b) {
+  DualF<N> r = a;
+  r.v -= b;
+  return r;
+}
+BY_DF operator-(float a, const DualF<N>& b) {
+  DualF<N> r;
+  r.v = a - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -b.d[k];
+  return r;
+}
+BY_DF operator*(const DualF<N>& a, float b) {
+  DualF<N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+BY_DF operator*(float a, const DualF<N>& b) { return b * a; }
+BY_DF operator/(const DualF<N>& a, float b) { return a * (1.0f / b); }
+BY_DF operator/(float a, const DualF<N>& b) {
+  DualF<N> r;
+  const float inv = 1.0f / b.v;
+  r.v = a * inv;
+  const float g = -r.v * inv;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = g * b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualF<N> dchain(const DualF<N>& a, float fv, float g) {
+  DualF<N> r;
+  r.v = fv;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = g * a.d[k];
+  return r;
+}
+
+// ------------------------------------------------------- math, float + dual --
+__device__ __forceinline__ float xsqrt(float x) { return sqrtf(x); }
+BY_DF xsqrt(const DualF<N>& a) {
+  const float s = sqrtf(a.v);
+  return dchain(a, s, s > 0.f ? 0.5f / s : 0.f);
+}
+__device__ __forceinline__ float xexp(float x) { return expf(x); }
+BY_DF xexp(const DualF<N>& a) {
+  const float e = expf(a.v);
+  return dchain(a, e, e);
+}
+__device__ __forceinline__ float xlog(float x) { return logf(x); }
+BY_DF xlog(const DualF<N>& a) { return dchain(a, logf(a.v), 1.0f / a.v); }
+__device__ __forceinline__ float xatan2(float y, float x) { return atan2f(y, x); }
+template <int N>
+__device__ __forceinline__ DualF<N> xatan2(const DualF<N>& y, const DualF<N>& x) {
+  DualF<N> r;
+  r.v = atan2f(y.v, x.v);
+  const float inv = 1.0f / (x.v * x.v + y.v * y.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = (x.v * y.d[k] - y.v * x.d[k]) * inv;
+  return r;
+}
+__device__ __forceinline__ void xsincos(float x, float* s, float* c) { sincosf(x, s, c); }
+template <int N>
+__device__ __forceinline__ void xsincos(const DualF<N>& x, DualF<N>* s, DualF<N>* c) {
+  float sv, cv;
+  sincosf(x.v, &sv, &cv);
+  *s = dchain(x, sv, cv);
+  *c = dchain(x, cv, -sv);
+}
+// sin and cos of 2 pi t (t in turns); the pi-scaled form reduces exactly.
+__device__ __forceinline__ void xsincos_turns(float t, float* s, float* c) {
+  sincospif(2.0f * t, s, c);
+}
+template <int N>
+__device__ __forceinline__ void xsincos_turns(const DualF<N>& t, DualF<N>* s, DualF<N>* c) {
+  float sv, cv;
+  sincospif(2.0f * t.v, &sv, &cv);
+  *s = dchain(t, sv, 2.0f * kPi * cv);
+  *c = dchain(t, cv, -2.0f * kPi * sv);
+}
+template <class S> __device__ __forceinline__ S xmax0(const S& a) { return vf(a) < 0.f ? S(0.f) : a; }
+
+// ----------------------------------------------------------------- vectors --
+template <class S>
+struct V3 {
+  S x, y, z;
+};
+template <class S> __device__ __forceinline__ V3<S> mk3(const S& x, const S& y, const S& z) {
+  V3<S> r;
+  r.x = x; r.y = y; r.z = z;
+  return r;
+}
+template <class S> __device__ __forceinline__ V3<S> lift3(float x, float y, float z) {
+  return mk3<S>(S(x), S(y), S(z));
+}
+template <class S> __device__ __forceinline__ V3<S> operator+(const V3<S>& a, const V3<S>& b) {
+  return mk3<S>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <class S> __device__ __forceinline__ V3<S> operator-(const V3<S>& a, const V3<S>& b) {
+  return mk3<S>(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+template <class S> __device__ __forceinline__ V3<S> operator-(const V3<S>& a) {
+  return mk3<S>(-a.x, -a.y, -a.z);
+}
+template <class S, class T> __device__ __forceinline__ V3<S> operator*(const V3<S>& a, const T& s) {
+  return mk3<S>(a.x * s, a.y * s, a.z * s);
+}
+template <class S> __device__ __forceinline__ S dot(const V3<S>& a, const V3<S>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <class S> __device__ __forceinline__ V3<S> cross(const V3<S>& a, const V3<S>& b) {
+  return mk3<S>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+template <class S> __device__ __forceinline__ V3<S> normalize(const V3<S>& a) {
+  return a * (S(1.0f) / xsqrt(dot(a, a)));
+}
+
+}  // namespace bysdf

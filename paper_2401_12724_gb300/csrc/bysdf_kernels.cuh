@@ -1,0 +1,309 @@
+// Kernel-side plumbing of libbysdf: launch arguments, TMA bulk copies of the
+// material table into shared memory with bounded mbarrier waits, record
+// loads, the warp-granular tile queue, and the per-record drivers.
+#pragma once
+
+#include "bysdf_model.cuh"
+
+namespace bysdf {
+
+enum : int { OPF_EVAL = 1, OPF_SAMPLE = 2, OPF_PDF = 4 };
+enum : int { MODE_ALL_SMEM = 0, MODE_SORTED = 1 };
+enum : uint32_t { ERR_TABLE_WAIT = 1u, ERR_TABLE_INFLIGHT = 2u };
+
+// Workspace layout (bytes): [0, 256) control words, then tile_start[n_mat + 1]
+// (int32), then per-tile gradient partials (deterministic backward).
+constexpr size_t kWsCtl = 256;
+struct WsCtl {
+  int32_t tile_counter;
+  uint32_t err;
+  int32_t pad[62];
+};
+
+struct KArgs {
+  const uint8_t* table;  // device material table (n_mat blocks of `stride` bytes)
+  int32_t n_mat;
+  int32_t stride;
+  int32_t mode;
+  int32_t tile;          // records per warp tile (32 * items)
+  int64_t n;
+  int64_t n_tiles;
+  const float *h, *u, *v, *wi, *wo, *ratio, *u0, *u1;
+  const int32_t* mat_id;
+  const int64_t* seg;
+  float *f_rgb, *pdf;
+  uint8_t* status;
+  float *wo_s, *weight_s, *pdf_s;
+  uint8_t* lstat_s;
+  const float* grad_f;
+  float* grad_params;
+  float* partials;       // deterministic backward: [n_tiles][8]
+  WsCtl* ctl;
+  const int32_t* tile_start;
+};
+
+// ------------------------------------------------------ TMA + mbarrier ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> shared (TMA), completion signalled on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls (each poll may itself suspend
+// for a hardware-defined interval), records the failure and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, WsCtl* ctl,
+                                                  uint32_t code) {
+  const uint32_t limit = 1u << 22;
+  for (uint32_t it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(&ctl->err, code);
+  return false;
+}
+
+// ------------------------------------------------------------ record IO ----
+__device__ __forceinline__ void load_record(const KArgs& a, int64_t i, bool need_wo,
+                                            bool need_u, Record& q) {
+  const int64_t n = a.n;
+  q.h = __ldg(a.h + i);
+  q.u = __ldg(a.u + i);
+  q.v = __ldg(a.v + i);
+  q.wi[0] = __ldg(a.wi + i);
+  q.wi[1] = __ldg(a.wi + n + i);
+  q.wi[2] = __ldg(a.wi + 2 * n + i);
+  if (need_wo) {
+    q.wo[0] = __ldg(a.wo + i);
+    q.wo[1] = __ldg(a.wo + n + i);
+    q.wo[2] = __ldg(a.wo + 2 * n + i);
+  } else {
+    q.wo[0] = q.wo[1] = q.wo[2] = 0.f;
+  }
+  q.ratio = a.ratio ? __ldg(a.ratio + i) : 0.f;
+  if (need_u) {
+    q.u0 = __ldg(a.u0 + i);
+    q.u1 = __ldg(a.u1 + i);
+  } else {
+    q.u0 = q.u1 = 0.f;
+  }
+}
+
+// Forward pass of one record: eval/pdf at hits->wo and/or one sample.
+template <int OP>
+__device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
+                                               const float2* map, int64_t i, Record& q) {
+  constexpr bool kEval = (OP & (OPF_EVAL | OPF_PDF)) != 0;
+  constexpr bool kSample = (OP & OPF_SAMPLE) != 0;
+  const int64_t n = a.n;
+  // eval needs a valid omega_o, sampling valid random numbers; in the fused
+  // op an invalid one invalidates only its own half
+  const bool base = base_valid(q, a.n_mat, a.ratio != nullptr);
+  const bool eval_ok = base && (!kEval || unit_ok(q.wo));
+  const bool samp_ok = base && (!kSample || u_valid(q));
+  int st = ST_INVALID;
+  Geo<float> G;
+  Shade<float> s;
+  if (eval_ok || samp_ok) {
+    const MatVars<float> mv = mat_vars<float>(m);
+    geometry(m, map, mv, q, G);
+    st = G.status;
+    if (st == ST_OK) make_shade(m, mv, G, q, s);
+  }
+  if constexpr (kEval) {
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, p = 0.f;
+    const int est = eval_ok ? st : ST_INVALID;
+    if (est == ST_OK) {
+      LobeVals<float> L;
+      eval_lobes(m, s, mk3<float>(q.wo[0], q.wo[1], q.wo[2]), L);
+      f0 = L.spec + m.alb[0] * L.body;
+      f1 = L.spec + m.alb[1] * L.body;
+      f2 = L.spec + m.alb[2] * L.body;
+      p = total_pdf(m, s, L);
+    }
+    if (OP & OPF_EVAL) {
+      __stcs(a.f_rgb + i, f0);
+      __stcs(a.f_rgb + n + i, f1);
+      __stcs(a.f_rgb + 2 * n + i, f2);
+    }
+    if (a.pdf) __stcs(a.pdf + i, p);
+    a.status[i] = (uint8_t)est;
+  }
+  if constexpr (kSample) {
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, ww0 = 0.f, ww1 = 0.f, ww2 = 0.f, p = 0.f;
+    int sst = samp_ok ? st : ST_INVALID, lobe = 0;
+    if (sst == ST_NO_HIT) {
+      w0 = -q.wi[0];
+      w1 = -q.wi[1];
+      w2 = -q.wi[2];
+      ww0 = ww1 = ww2 = 1.f;
+    } else if (sst == ST_OK) {
+      V3<float> wo;
+      sst = ST_BAD_SAMPLE;
+      if (sample_dir(m, s, q.u0, q.u1, &wo, &lobe)) {
+        w0 = wo.x;
+        w1 = wo.y;
+        w2 = wo.z;
+        LobeVals<float> L;
+        eval_lobes(m, s, wo, L);
+        const float pt = total_pdf(m, s, L);
+        if (pt > 0.f) {
+          const float ip = 1.0f / pt;
+          ww0 = (L.spec + m.alb[0] * L.body) * ip;
+          ww1 = (L.spec + m.alb[1] * L.body) * ip;
+          ww2 = (L.spec + m.alb[2] * L.body) * ip;
+          p = pt;
+          sst = ST_OK;
+        }
+      }
+    }
+    __stcs(a.wo_s + i, w0);
+    __stcs(a.wo_s + n + i, w1);
+    __stcs(a.wo_s + 2 * n + i, w2);
+    __stcs(a.weight_s + i, ww0);
+    __stcs(a.weight_s + n + i, ww1);
+    __stcs(a.weight_s + 2 * n + i, ww2);
+    __stcs(a.pdf_s + i, p);
+    a.lstat_s[i] = (uint8_t)(sst | (lobe << 4));
+  }
+}
+
+// Gradient of sum_c g_c f_c of one record w.r.t. the 8 material parameters.
+__device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
+                                                const float2* map, int64_t i, Record& q,
+                                                float gout[8]) {
+  typedef DualF<ND> D;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gout[k] = 0.f;
+  if (!record_valid(q, a.n_mat, true, a.ratio != nullptr, false)) return;
+  const MatVars<D> mv = mat_vars<D>(m);
+  Geo<D> G;
+  geometry(m, map, mv, q, G);
+  if (G.status != ST_OK) return;
+  Shade<D> s;
+  make_shade(m, mv, G, q, s);
+  LobeVals<D> L;
+  eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L);
+  const int64_t n = a.n;
+  const float g0 = __ldg(a.grad_f + i), g1 = __ldg(a.grad_f + n + i),
+              g2 = __ldg(a.grad_f + 2 * n + i);
+  // f_c = spec + albedo_c body: closed form in the albedo, duals elsewhere
+  const float gs = g0 + g1 + g2;
+  const float gb = g0 * m.alb[0] + g1 * m.alb[1] + g2 * m.alb[2];
+  gout[0] = g0 * L.body.v;
+  gout[1] = g1 * L.body.v;
+  gout[2] = g2 * L.body.v;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) gout[3 + k] = gs * L.spec.d[k] + gb * L.body.d[k];
+}
+
+// Shared-memory staging of the material tables and the warp tile loop, common
+// to the forward and backward persistent kernels.
+//
+// MODE_ALL_SMEM: every table is copied once per CTA by one TMA bulk copy;
+//   records may come in any material order.
+// MODE_SORTED:   records are grouped by material; each warp owns one table
+//   slot and refills it (TMA bulk copy) when its tile's material changes.
+// Work is handed out one warp tile (32 * items records) at a time from an
+// atomic counter, so warps that drew cheap records take more tiles.
+template <int BLOCK, class Body>
+__device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, uint64_t* bars,
+                                                Body&& body) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ int s_ok;
+  if (a.mode == MODE_ALL_SMEM) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      fence_mbar_init();
+      const uint32_t bytes = (uint32_t)a.n_mat * (uint32_t)a.stride;
+      mbar_arrive_tx(&bars[0], bytes);
+      bulk_g2s(smem, a.table, bytes, &bars[0]);
+      int ok = mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_WAIT);
+      if (!ok) mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_INFLIGHT);
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+  } else {
+    if (lane == 0) {
+      mbar_init(&bars[warp], 1);
+      fence_mbar_init();
+    }
+    __syncwarp();
+  }
+  const int64_t n_tiles = a.mode == MODE_SORTED ? (int64_t)__ldg(a.tile_start + a.n_mat)
+                                                : a.n_tiles;
+  uint8_t* slot = smem + (size_t)warp * a.stride;
+  uint32_t parity = 0;
+  int cur = -1;
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = atomicAdd(&a.ctl->tile_counter, 1);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= n_tiles) break;
+    int64_t begin, end;
+    int mat = -1;
+    if (a.mode == MODE_ALL_SMEM) {
+      begin = (int64_t)tile * a.tile;
+      end = begin + a.tile < a.n ? begin + a.tile : a.n;
+    } else {
+      int lo = 0, hi = a.n_mat;  // last material whose first tile <= tile
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid;
+      }
+      mat = lo;
+      const int64_t s1 = __ldg(a.seg + mat + 1);
+      begin = __ldg(a.seg + mat) + (int64_t)(tile - __ldg(a.tile_start + mat)) * a.tile;
+      end = begin + a.tile < s1 ? begin + a.tile : s1;
+      if (mat != cur) {
+        __syncwarp();
+        if (lane == 0) {
+          fence_proxy_async();
+          mbar_arrive_tx(&bars[warp], (uint32_t)a.stride);
+          bulk_g2s(slot, a.table + (size_t)mat * a.stride, (uint32_t)a.stride, &bars[warp]);
+        }
+        bool ok = mbar_wait_bounded(&bars[warp], parity, a.ctl, ERR_TABLE_WAIT);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+          if (lane == 0) mbar_wait_bounded(&bars[warp], parity, a.ctl, ERR_TABLE_INFLIGHT);
+          break;
+        }
+        parity ^= 1u;
+        cur = mat;
+      }
+    }
+    body(begin, end, mat, slot, lane, tile);
+  }
+}
+
+}  // namespace bysdf

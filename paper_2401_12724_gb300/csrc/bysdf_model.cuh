@@ -1,0 +1,556 @@
+// Per-record yarn BYSDF model (device).  One implementation, generic in the
+// scalar type S: float for eval / sample / pdf, DualF<ND> for the backward.
+//
+// Steps (Khattar et al.):
+//   entry ray from (h, u, omega_i)          Sec. 3.3 (reading: in-plane angle
+//                                           asin h from -n_u, slope from omega_i)
+//   implicit ply trace, N_it updates         Sec. 3.4
+//   ply frame, fiber frame from 1D maps      Sec. 3.4, 3.5.1
+//   G_p (in-plane chords through the other   Sec. 4.1.4
+//   plies), G_f (fiber map)
+//   footprint nodes and aggregation          Sec. 4.2 Eqs. 8-11, Sec. 5.3
+//   lobes f_x^S, f_y^S, f_x^B, f_y^B         Sec. 4.1 Eqs. 1-6, tau^{N_i} Eq. 4
+//   sampling, pdf                            Sec. 4.1.5
+#pragma once
+
+#include "bysdf_common.cuh"
+
+namespace bysdf {
+
+enum { ST_OK = 0, ST_NO_HIT = 1, ST_INVALID = 2, ST_BAD_SAMPLE = 3 };
+
+struct Record {
+  float h, u, v, ratio;
+  float wi[3], wo[3];
+  float u0, u1;
+  int mat;
+};
+
+// frac(k * v) for a rate k = hi + lo held as two floats: the product is
+// formed exactly (FMA residual) before the integer part is dropped, so a
+// phase of hundreds of turns keeps float precision in its fraction.
+__device__ __forceinline__ float frac_prod(float hi, float lo, float v) {
+  const float p = __fmul_rn(hi, v);
+  float e = fmaf(hi, v, -p);
+  e = fmaf(lo, v, e);
+  return __fadd_rn(__fsub_rn(p, rintf(p)), e);
+}
+
+// Differentiable per-material quantities.
+template <class S>
+struct MatVars {
+  S kp, kf;             // ply turns / length, fiber map periods / length
+  S cos_af, sin_af;     // fiber helix angle
+  S sigma_s;            // shadow density
+  S beta_t, beta_b;     // GGX roughness (radians)
+};
+
+template <class S>
+__device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m) {
+  MatVars<S> q;
+  q.kp = S(m.kp_hi + m.kp_lo);
+  q.kf = S(m.kf_hi + m.kf_lo);
+  q.cos_af = S(m.cos_af);
+  q.sin_af = S(m.sin_af);
+  q.sigma_s = S(m.sigma_s);
+  q.beta_t = S(m.beta_t);
+  q.beta_b = S(m.beta_b);
+  if constexpr (is_dual<S>::value) {
+    q.kp.d[D_ALPHA_P] = m.dkp;
+    q.kf.d[D_ALPHA_F] = m.dkf;
+    q.cos_af.d[D_ALPHA_F] = -m.sin_af;
+    q.sin_af.d[D_ALPHA_F] = m.cos_af;
+    q.sigma_s.d[D_SIGMA_S] = 1.f;
+    q.beta_t.d[D_BETA_T] = 1.f;
+    q.beta_b.d[D_BETA_B] = 1.f;
+  }
+  return q;
+}
+
+// frac(k v) with the tangent of k v (the value is the compensated one).
+template <class S>
+__device__ __forceinline__ S frac_prod_s(const S& k, float hi, float lo, float v) {
+  if constexpr (is_dual<S>::value) {
+    S r = k * v;
+    r.v = frac_prod(hi, lo, v);
+    return r;
+  } else {
+    return frac_prod(hi, lo, v);
+  }
+}
+
+// ------------------------------------------------------------ validation --
+__device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
+
+__device__ __forceinline__ bool unit_ok(const float* w) {
+  if (!finitef(w[0]) || !finitef(w[1]) || !finitef(w[2])) return false;
+  const float nn = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  return fabsf(nn - 1.0f) <= 1e-3f;
+}
+// Inputs every op needs: (h, u, v, omega_i, material id, ratio).
+__device__ __forceinline__ bool base_valid(const Record& q, int n_mat, bool has_ratio) {
+  if (!finitef(q.h) || !finitef(q.u) || !finitef(q.v)) return false;
+  if (fabsf(q.h) > 1.0f) return false;
+  if (!unit_ok(q.wi)) return false;
+  if (q.mat < 0 || q.mat >= n_mat) return false;
+  if (has_ratio && !(q.ratio >= 0.0f && finitef(q.ratio))) return false;
+  return true;
+}
+__device__ __forceinline__ bool u_valid(const Record& q) {
+  return q.u0 >= 0.0f && q.u0 < 1.0f && q.u1 >= 0.0f && q.u1 < 1.0f;
+}
+__device__ __forceinline__ bool record_valid(const Record& q, int n_mat, bool need_wo,
+                                             bool has_ratio, bool need_u) {
+  return base_valid(q, n_mat, has_ratio) && (!need_wo || unit_ok(q.wo)) &&
+         (!need_u || u_valid(q));
+}
+
+// ------------------------------------------------------------- footprint --
+// Sec. 4.2 / 5.3 (reading): ratio is the half-width of [h1, h2] in h units;
+// K = ceil(K_max (h2 - h1) / 2) midpoint nodes.  Decided in float with
+// explicitly rounded operations (no contraction), as the oracle decides it.
+struct Footprint {
+  float h1, width;
+  int K;
+};
+__device__ __forceinline__ Footprint footprint(float h0, float ratio, int kmax) {
+  Footprint f;
+  const float a = __fsub_rn(h0, ratio);
+  const float b = __fadd_rn(h0, ratio);
+  f.h1 = a < -1.0f ? -1.0f : a;
+  const float h2 = b > 1.0f ? 1.0f : b;
+  f.width = __fsub_rn(h2, f.h1);
+  const float kf = __fmul_rn((float)kmax * 0.5f, f.width);
+  int K = (int)ceilf(kf);
+  f.K = K < 1 ? 1 : (K > kmax ? kmax : K);
+  return f;
+}
+
+// ------------------------------------------------------------- geometry --
+template <class S>
+struct NodeGeo {
+  bool hit;
+  int ni;
+  V3<S> x, nf, tf;
+  S g;  // G_p * G_f
+};
+
+// Sec. 3.5.1: periodic linear interpolation of the tabulated maps; w is the
+// fiber phase in map periods.
+template <class S>
+__device__ __forceinline__ void fiber_lookup(const float2* map, int T, const S& w, S* delta,
+                                             S* of) {
+  const float wv = vf(w) + 0.5f;
+  const S a = w + (0.5f - floorf(wv));
+  const S tau = a * (float)T - 0.5f;
+  const float fl = floorf(vf(tau));
+  const S f = tau - fl;
+  int i0 = (int)fl;
+  i0 = i0 < 0 ? i0 + T : (i0 >= T ? i0 - T : i0);
+  const int i1 = i0 + 1 == T ? 0 : i0 + 1;
+  const float2 t0 = map[i0], t1 = map[i1];
+  *delta = t0.x + f * (t1.x - t0.x);
+  *of = t0.y + f * (t1.y - t0.y);
+}
+
+// One footprint node: the camera ray enters at in-plane point X0 with
+// in-plane unit direction e and longitudinal slope kappa (Sec. 3.4).
+template <class S>
+__device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
+                                              const MatVars<S>& mv, float X0x, float X0y,
+                                              float ex, float ey, float v, float kappa,
+                                              float wx, float wy, const S& turns_v,
+                                              const S& phase_f_v, NodeGeo<S>& out) {
+  const float Rp = m.Rp, Rc = m.Rc;
+  out.hit = false;
+  out.ni = 0;
+  int best = -1;
+  S best_t = S(0.f), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
+  for (int k = 0; k < m.np; ++k) {
+    // cross-section update: ply centre at the height of the current
+    // intersection, 2D ray / circle intersection there, repeat
+    const S turns0 = turns_v + (float)k * m.inv_np;
+    S t = S(0.f), cx = S(0.f), cy = S(0.f), sp = S(0.f), cp = S(1.f);
+    bool hit = true;
+    for (int n = 0; n < m.nit; ++n) {
+      const S turns = turns0 + mv.kp * (kappa * t);
+      xsincos_turns(turns, &sp, &cp);
+      cx = Rc * cp;
+      cy = Rc * sp;
+      const S qx = X0x - cx, qy = X0y - cy;
+      const S b = qx * ex + qy * ey;
+      const S perp = qx * ey - qy * ex;
+      const S disc = (Rp - perp) * (Rp + perp);
+      if (vf(disc) < 0.f) {
+        hit = false;
+        break;
+      }
+      const S tn = xmax0(-b - xsqrt(disc));
+      if constexpr (!is_dual<S>::value) {
+        // a repeated iterate is a fixed point: every further update returns it
+        if (tn == t) break;
+      }
+      t = tn;
+    }
+    if (!hit) continue;
+    out.ni += 1;
+    if (best < 0 || vf(t) < vf(best_t)) {
+      best = k;
+      best_t = t;
+      best_cx = cx;
+      best_cy = cy;
+      best_s = sp;
+      best_c = cp;
+    }
+  }
+  if (best < 0) return;
+  out.hit = true;
+  // Sec. 3.4: hit point, ply normal (from the ply centre, in the circular
+  // cross-section), ply tangent (derivative of the helix through x)
+  const S xx = X0x + best_t * ex, xy = X0y + best_t * ey;
+  const S dz = kappa * best_t;
+  out.x = mk3<S>(xx, xy, v + dz);
+  const S dx = xx - best_cx, dy = xy - best_cy;
+  const S inv_dl = S(1.f) / xsqrt(dx * dx + dy * dy);
+  const V3<S> np = mk3<S>(dx * inv_dl, dy * inv_dl, S(0.f));
+  const S wp = (2.0f * kPi) * mv.kp;
+  const V3<S> traw = mk3<S>(-(wp * xy), wp * xx, S(1.f));
+  const V3<S> tp = normalize(traw - np * dot(traw, np));
+  const V3<S> ep = cross(tp, np);
+  // Sec. 3.5.1: ply azimuth of the hit about the ply centre, from the ply
+  // centre's radial direction; fiber phase in map periods; 1D map lookup
+  const S u_ply = xatan2(best_c * np.y - best_s * np.x, best_c * np.x + best_s * np.y);
+  const S w = u_ply * m.m_over_2pi - phase_f_v - mv.kf * dz;
+  S delta, of;
+  fiber_lookup(map, m.T, w, &delta, &of);
+  // n_f = n'(R(n_p)), t_f = t'(R(t_p))
+  out.tf = tp * mv.cos_af + ep * mv.sin_af;
+  S sd, cd;
+  xsincos(delta, &sd, &cd);
+  out.nf = np * cd + cross(out.tf, np) * sd;
+  // Sec. 4.1.4: ply shadowing by the in-plane chords through the other
+  // plies of this cross-section; fiber shadowing from the map
+  S occ = S(0.f);
+  for (int j = 1; j < m.np; ++j) {
+    int r = j;
+    const float rc = m.rot_c[r], rs = m.rot_s[r];
+    const S cjx = best_cx * rc - best_cy * rs, cjy = best_cx * rs + best_cy * rc;
+    const S qx = xx - cjx, qy = xy - cjy;
+    const S b = qx * wx + qy * wy;
+    const S perp = qx * wy - qy * wx;
+    const S disc = (Rp - perp) * (Rp + perp);
+    if (vf(disc) > 0.f) {
+      const S sq = xsqrt(disc);
+      const S s2 = sq - b;
+      if (vf(s2) > 0.f) occ = occ + (s2 - xmax0(-b - sq));
+    }
+  }
+  out.g = xexp(-(mv.sigma_s * (occ * m.inv_2Rp + of)));
+}
+
+// Aggregated geometry of a record (Sec. 4.2 Eqs. 8-11, W = 1).
+template <class S>
+struct Geo {
+  int status;
+  float width;
+  V3<S> n, t, x;
+  S g, ni;
+};
+
+template <class S>
+__device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
+                                         const MatVars<S>& mv, const Record& q,
+                                         Geo<S>& G) {
+  G.status = ST_NO_HIT;
+  const Footprint fp = footprint(q.h, q.ratio, m.kmax);
+  G.width = fp.width;
+  const float g0 = asinf(q.h);
+  const float u_rel = q.u - g0;
+  float su, cu;
+  sincosf(u_rel, &su, &cu);
+  const float ex = -cu, ey = -su;
+  const float lxy = sqrtf(q.wi[0] * q.wi[0] + q.wi[1] * q.wi[1]);
+  if (!(lxy >= 1e-7f)) return;
+  const float inv_l = 1.0f / lxy;
+  const float kappa = -q.wi[2] * inv_l;
+  const float wx = q.wi[0] * inv_l, wy = q.wi[1] * inv_l;
+  const S turns_v = frac_prod_s(mv.kp, m.kp_hi, m.kp_lo, q.v);
+  const S phase_f_v = frac_prod_s(mv.kf, m.kf_hi, m.kf_lo, q.v);
+  V3<S> ns = lift3<S>(0.f, 0.f, 0.f), ts = ns, xs = ns;
+  S gs = S(0.f);
+  int nis = 0, nhit = 0;
+  const bool near = fp.K == 1 && fp.width == 0.0f;
+  for (int j = 0; j < fp.K; ++j) {
+    float X0x, X0y;
+    if (near) {
+      sincosf(q.u, &X0y, &X0x);
+    } else {
+      const float hj = fp.h1 + ((float)j + 0.5f) * fp.width / (float)fp.K;
+      sincosf(u_rel + asinf(hj), &X0y, &X0x);
+    }
+    X0x *= m.R;
+    X0y *= m.R;
+    NodeGeo<S> nd;
+    node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, turns_v, phase_f_v, nd);
+    if (!nd.hit) continue;
+    nhit += 1;
+    nis += nd.ni;
+    ns = ns + nd.nf;
+    ts = ts + nd.tf;
+    xs = xs + nd.x;
+    gs = gs + nd.g;
+  }
+  if (nhit == 0) return;
+  const float inv = 1.0f / (float)nhit;
+  const S nl = xsqrt(dot(ns, ns));
+  if (!(vf(nl) > 1e-9f * (float)nhit)) return;
+  G.n = ns * (S(1.f) / nl);
+  const V3<S> tperp = ts - G.n * dot(ts, G.n);
+  const S tl = xsqrt(dot(tperp, tperp));
+  if (!(vf(tl) > 1e-9f * (float)nhit)) return;
+  G.t = tperp * (S(1.f) / tl);
+  G.x = xs * inv;
+  G.g = gs * inv;
+  G.ni = S((float)nis * inv);
+  G.status = ST_OK;
+}
+
+// ------------------------------------------------------------ microfacet --
+// Unpolarised dielectric Fresnel reflectance, eta = eta_t / eta_i, cos >= 0.
+template <class S>
+__device__ __forceinline__ S fresnel(const S& ci, float eta) {
+  const S s2t = (1.0f - ci * ci) * (1.0f / (eta * eta));
+  if (!(vf(s2t) < 1.0f)) return S(1.f);
+  const S ct = xsqrt(1.0f - s2t);
+  const S rs = (ci - eta * ct) / (ci + eta * ct);
+  const S rp = (eta * ci - ct) / (eta * ci + ct);
+  return 0.5f * (rs * rs + rp * rp);
+}
+// Anisotropic GGX (Heitz 2014) in a local frame (x = t, y = b, z = n).
+template <class S>
+__device__ __forceinline__ S ggx_d(const V3<S>& m, const S& at, const S& ab) {
+  if (!(vf(m.z) > 0.f)) return S(0.f);
+  const S mx = m.x / at, my = m.y / ab;
+  const S q = mx * mx + my * my + m.z * m.z;
+  return S(1.0f / kPi) / (at * ab * q * q);
+}
+template <class S>
+__device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, const S& at, const S& ab) {
+  if (!(vf(wm) * vf(w.z) > 0.f)) return S(0.f);
+  const S an = vf(w.z) < 0.f ? -w.z : w.z;
+  const S ax = at * w.x, ay = ab * w.y;
+  return 2.0f * an / (an + xsqrt(an * an + ax * ax + ay * ay));
+}
+// GGX visible-normal sample (Heitz 2018), local frame, w.z > 0.
+template <class S>
+__device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, const S& at, const S& ab,
+                                             float u0, float u1) {
+  const V3<S> V = normalize(mk3<S>(at * w.x, ab * w.y, w.z));
+  const S lensq = V.x * V.x + V.y * V.y;
+  V3<S> T1 = lift3<S>(1.f, 0.f, 0.f);
+  if (vf(lensq) > 0.f) {
+    const S il = S(1.f) / xsqrt(lensq);
+    T1 = mk3<S>(-(V.y * il), V.x * il, S(0.f));
+  }
+  const V3<S> T2 = cross(V, T1);
+  float sphi, cphi;
+  sincospif(2.0f * u1, &sphi, &cphi);
+  const float r = sqrtf(u0);
+  const float t1 = r * cphi;
+  const S s = 0.5f * (1.0f + V.z);
+  const S t2 = (1.0f - s) * sqrtf(1.0f - t1 * t1) + s * (r * sphi);
+  const S tz = xsqrt(xmax0(1.0f - t1 * t1 - t2 * t2));
+  const V3<S> Nh = T1 * t1 + T2 * t2 + V * tz;
+  return normalize(mk3<S>(at * Nh.x, ab * Nh.y, xmax0(Nh.z)));
+}
+
+template <class S>
+__device__ __forceinline__ V3<S> to_local(const V3<S>& w, const V3<S>& t, const V3<S>& b,
+                                          const V3<S>& n) {
+  return mk3<S>(dot(w, t), dot(w, b), dot(w, n));
+}
+
+// ---------------------------------------------------------------- shading --
+template <class S>
+struct Shade {
+  V3<S> t, b, n, wi;
+  S mui, at, ab, g, fr;
+  // transmission path (f_y^S)
+  bool tt_ok;
+  V3<S> iy, by, ny;
+  S tx, tau;
+};
+
+template <class S>
+__device__ __forceinline__ S clamp_alpha(const S& a) {
+  if (vf(a) < 1e-3f) return S(1e-3f);
+  if (vf(a) > 1.5f) return S(1.5f);
+  return a;
+}
+
+template <class S>
+__device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
+                                           const Geo<S>& G, const Record& q, Shade<S>& s) {
+  s.wi = lift3<S>(q.wi[0], q.wi[1], q.wi[2]);
+  s.n = G.n;
+  s.t = G.t;
+  s.b = cross(s.n, s.t);
+  // reading: two-sided shading, the side of omega_i is outside at x
+  if (vf(dot(s.wi, s.n)) < 0.f) {
+    s.n = -s.n;
+    s.b = -s.b;
+  }
+  s.mui = dot(s.wi, s.n);
+  // Sec. 4.2: beta_multi = beta + (h2 - h1) / 2 (reading), GGX alpha = beta
+  const float hw = 0.5f * G.width;
+  s.at = clamp_alpha(mv.beta_t + hw);
+  s.ab = clamp_alpha(mv.beta_b + hw);
+  s.g = G.g;
+  s.fr = fresnel(s.mui, m.eta);
+  s.tt_ok = false;
+  // Sec. 4.1.1 (reading): smooth refraction into the yarn at x, straight path
+  // to the yarn surface y, attenuation tau^{N_i} (Eq. 4)
+  const S s2t = (1.0f - s.mui * s.mui) * (m.inv_eta * m.inv_eta);
+  if (!(vf(s.mui) > 0.f) || !(vf(s2t) < 1.0f)) return;
+  const S ct = xsqrt(1.0f - s2t);
+  const V3<S> din = s.wi * (-m.inv_eta) + s.n * (s.mui * m.inv_eta - ct);
+  const S a = din.x * din.x + din.y * din.y;
+  if (!(vf(a) > 1e-12f)) return;
+  const S bq = G.x.x * din.x + G.x.y * din.y;
+  const S c = G.x.x * G.x.x + G.x.y * G.x.y - m.R * m.R;
+  const S disc = xmax0(bq * bq - a * c);
+  const S sy = xmax0((xsqrt(disc) - bq) / a);
+  const S yx = G.x.x + din.x * sy, yy = G.x.y + din.y * sy;
+  const S il = S(1.f) / xsqrt(yx * yx + yy * yy);
+  s.ny = mk3<S>(yx * il, yy * il, S(0.f));
+  s.by = mk3<S>(s.ny.y, -s.ny.x, S(0.f));  // n_y x z
+  s.iy = -din;
+  s.tau = xexp(-(m.sigma_t * G.ni * sy));
+  s.tx = 1.0f - s.fr;
+  s.tt_ok = true;
+}
+
+// f |wo.n| of the four lobes at wo; spec = f_x^S + f_y^S (grey), body = the
+// body lobes per unit albedo; pdf terms of the four sampling strategies.
+template <class S>
+struct LobeVals {
+  S spec, body, pR, pT, pxb, pyb;
+};
+
+template <class S>
+__device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, const V3<S>& wo,
+                                           LobeVals<S>& L) {
+  L.spec = S(0.f);
+  L.body = S(0.f);
+  L.pR = S(0.f);
+  L.pT = S(0.f);
+  L.pxb = S(0.f);
+  L.pyb = S(0.f);
+  if (!(vf(s.mui) > 0.f)) return;
+  const S muo = dot(wo, s.n);
+  if (vf(muo) > 0.f) {
+    // Eq. 2, reflection (Walter et al. 2007 with GGX)
+    const V3<S> h = normalize(s.wi + wo);
+    const S wih = dot(s.wi, h), woh = dot(wo, h);
+    const V3<S> hl = to_local(h, s.t, s.b, s.n);
+    const V3<S> il = to_local(s.wi, s.t, s.b, s.n);
+    const V3<S> ol = to_local(wo, s.t, s.b, s.n);
+    const S D = ggx_d(hl, s.at, s.ab);
+    const S g1i = ggx_g1(il, wih, s.at, s.ab);
+    const S g1o = ggx_g1(ol, woh, s.at, s.ab);
+    const S F = fresnel(wih, m.eta);
+    const S q = g1i * D / (4.0f * s.mui);
+    L.spec = m.ks * F * g1o * q;
+    L.pR = q;
+    // Eq. 5 with LS = 1 / (4 pi (mu_i + mu_o)), normalised to albedo r B G
+    const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + S(1.f) / s.mui));
+    const S br = (S(1.0f / (4.0f * kPi)) / (s.mui + muo) + 1.0f / kPi) / (1.0f + aLS);
+    L.body = m.r * m.B * s.g * br * muo;
+    L.pxb = muo * (1.0f / kPi);
+  } else if (vf(muo) < 0.f) {
+    // Eq. 6, forward body
+    L.body = (1.0f - m.r) * m.B * s.g * (1.0f / kPi) * (-muo);
+    L.pyb = -muo * (1.0f / kPi);
+    // Eq. 3: exit BTDF at y from inside (eta) to outside (1), times the entry
+    // transmittance and tau^{N_i}
+    if (s.tt_ok) {
+      const S ion = dot(s.iy, s.ny), oon = dot(wo, s.ny);
+      if (vf(ion) < 0.f && vf(oon) > 0.f) {
+        V3<S> ht = normalize(-(s.iy * m.eta + wo));
+        if (vf(dot(ht, s.ny)) < 0.f) ht = -ht;
+        const S ih = dot(s.iy, ht), oh = dot(wo, ht);
+        if (vf(ih) < 0.f && vf(oh) > 0.f) {
+          const S den = m.eta * ih + oh;
+          const V3<S> z = lift3<S>(0.f, 0.f, 1.f);
+          const V3<S> hl = to_local(ht, z, s.by, s.ny);
+          const V3<S> il = to_local(s.iy, z, s.by, s.ny);
+          const V3<S> ol = to_local(wo, z, s.by, s.ny);
+          const S D = ggx_d(hl, s.at, s.ab);
+          const S g1i = ggx_g1(il, ih, s.at, s.ab);
+          const S g1o = ggx_g1(ol, oh, s.at, s.ab);
+          const S Fy = fresnel(-ih, m.inv_eta);
+          const S q = g1i * (-ih) * D * oh / ((-ion) * den * den);
+          L.spec = m.ks * s.tx * s.tau * (1.0f - Fy) * g1o * q;
+          L.pT = q;
+        }
+      }
+    }
+  }
+}
+
+// Sec. 4.1.5: lobe probabilities (1 - B) F(mu_i), (1 - B)(1 - F), B r, B (1 - r).
+template <class S>
+__device__ __forceinline__ S total_pdf(const MatDev& m, const Shade<S>& s, const LobeVals<S>& L) {
+  const S PR = (1.0f - m.B) * s.fr;
+  const S PT = (1.0f - m.B) - PR;
+  return PR * L.pR + PT * L.pT + (m.B * m.r) * L.pxb + (m.B * (1.0f - m.r)) * L.pyb;
+}
+
+// Draw wo (Sec. 4.1.5).  Returns false when the sample leaves the lobe.
+__device__ __forceinline__ bool sample_dir(const MatDev& m, const Shade<float>& s, float u0,
+                                           float u1, V3<float>* wo, int* lobe) {
+  const float P[4] = {(1.0f - m.B) * s.fr, (1.0f - m.B) * (1.0f - s.fr), m.B * m.r,
+                      m.B * (1.0f - m.r)};
+  int k = 3;
+  float lo = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    if (k == 3 && u0 < lo + P[j]) {
+      k = j;
+    } else if (k == 3) {
+      lo += P[j];
+    }
+  }
+  *lobe = k;
+  float ur = P[k] > 0.f ? (u0 - lo) / P[k] : 0.f;
+  ur = fminf(fmaxf(ur, 0.0f), 0.99999994f);
+  if (k == 0) {
+    const V3<float> il = to_local(s.wi, s.t, s.b, s.n);
+    const V3<float> ml = vndf_sample(il, s.at, s.ab, ur, u1);
+    const V3<float> mw = s.t * ml.x + s.b * ml.y + s.n * ml.z;
+    *wo = mw * (2.0f * dot(s.wi, mw)) - s.wi;
+    return dot(*wo, s.n) > 0.f;
+  }
+  if (k == 1) {
+    if (!s.tt_ok) return false;
+    const V3<float> Nn = -s.ny;
+    const V3<float> Tn = mk3<float>(0.f, 0.f, 1.f);
+    const V3<float> Bn = cross(Nn, Tn);
+    const V3<float> il = to_local(s.iy, Tn, Bn, Nn);
+    const V3<float> ml = vndf_sample(il, s.at, s.ab, ur, u1);
+    const V3<float> mw = Tn * ml.x + Bn * ml.y + Nn * ml.z;
+    const float c = dot(s.iy, mw);
+    const float s2t = m.eta * m.eta * (1.0f - c * c);
+    if (!(c > 0.f) || !(s2t < 1.0f)) return false;
+    *wo = normalize(s.iy * (-m.eta) + mw * (m.eta * c - sqrtf(1.0f - s2t)));
+    return dot(*wo, s.ny) > 0.f && dot(*wo, s.n) < 0.f;
+  }
+  float sphi, cphi;
+  sincospif(2.0f * u1, &sphi, &cphi);
+  const float r = sqrtf(ur);
+  const float zc = sqrtf(fmaxf(0.f, 1.0f - ur)) * (k == 2 ? 1.0f : -1.0f);
+  *wo = s.t * (r * cphi) + s.b * (r * sphi) + s.n * zc;
+  return true;
+}
+
+}  // namespace bysdf

@@ -1,0 +1,266 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on seeded inputs shaped like the five workloads, at sizes
+the oracle finishes in seconds (several warp tiles plus a ragged tail), and
+on sampled records of the full-size workloads in the benchmark's launch
+configuration.  See parity_util for the tolerance and the conditioning rule."""
+import numpy as np
+import pytest
+
+import parity_util as PU
+from paper_2401_12724_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_12724_gb300 import api as A
+    return A
+
+
+def dev(api, rec, seg=None):
+    return api.records_to_device(rec, "cuda", seg)
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def check_eval(orc, api, mats_desc, rec, seg=None, name="eval", max_ill=0.03):
+    M = api.Materials(mats_desc)
+    d = dev(api, rec, seg)
+    f, p, st = api.eval(M, d)
+    torch.cuda.synchronize()
+    f, p, st = np_(f), np_(p), np_(st)
+    fn = lambda r: orc.eval_records(mats_desc, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, rec)
+    good = PU.split_conditioned([fb, pb], [(q[0], q[1]) for q in pert], sb, [q[2] for q in pert])
+    assert np.array_equal(st[good], sb[good]), f"{name}: status differs on well-conditioned records"
+    r1 = PU.assert_close_conditioned(f, fb, [q[0] for q in pert], good, name + ".f", max_ill)
+    r2 = PU.assert_close_conditioned(p, pb, [q[1] for q in pert], good, name + ".pdf", max_ill)
+    assert M.workspace_error() == 0
+    return M, d, (f, p, st), (fb, pb, sb), good, (r1, r2)
+
+
+def test_eval_near_field_one_material(orc, api):
+    rec = I.records(1, 0, 20011)
+    _, _, (f, p, st), _, good, stats = check_eval(orc, api, I.materials(1), rec, name="c1")
+    assert (st == 0).mean() > 0.7 and (st == 1).any()
+
+
+def test_eval_sample_pdf_eight_materials(orc, api):
+    mats = I.materials(2)
+    rec = I.records(2, 0, 12007)
+    M, d, (f, p, st), (fb, pb, sb), good, _ = check_eval(orc, api, mats, rec, name="c2")
+    # pdf-only call equals the eval call's pdf
+    p2, st2 = api.pdf(M, d)
+    np.testing.assert_allclose(np_(p2), p, rtol=1e-6, atol=1e-7)
+    assert np.array_equal(np_(st2), st)
+    # sampling against the oracle with identical random numbers
+    wo, w, ps, ls = api.sample(M, d)
+    wo, w, ps, ls = np_(wo), np_(w), np_(ps), np_(ls)
+    fn = lambda r: orc.sample_records(mats, r, threads=8)  # noqa: E731
+    base, pert = PU.conditioning(fn, rec, sample=True)
+    wob, wb, pb_s, sb_s, lb = base
+    code_b = sb_s | (lb << 4)
+    good = PU.split_conditioned([wob, wb, pb_s], [(q[0], q[1], q[2]) for q in pert], code_b,
+                                [q[3] | (q[4] << 4) for q in pert])
+    assert np.array_equal(ls[good], code_b[good]), "sample: lobe/status differ"
+    ok = good & (sb_s == 0)
+    ang = PU.angle_between(wo[:, ok], wob[:, ok])
+    assert ang.max() <= PU.ANGLE, f"sampled direction off by {ang.max():.3g} rad"
+    PU.assert_close_conditioned(w, wb, [q[1] for q in pert], good, "sample.weight")
+    PU.assert_close_conditioned(ps, pb_s, [q[2] for q in pert], good, "sample.pdf")
+    # fused call == separate calls
+    o = api.eval_sample_pdf(M, d)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(np_(o["f"]), f, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(np_(o["pdf"]), p, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(np_(o["weight"]), w, rtol=1e-6, atol=1e-7)
+    assert np.array_equal(np_(o["lobe_status"]), ls) and np.array_equal(np_(o["status"]), st)
+
+
+def test_multiscale_footprints(orc, api):
+    rec = I.records(3, 0, 6007)
+    check_eval(orc, api, I.materials(3), rec, name="c3")
+    # far field: any ratio beyond 1 + |h| gives the same value
+    M = api.Materials(I.materials(3))
+    r2 = dict(rec)
+    r2["ratio"] = np.full(len(rec["h"]), 100.0, np.float32)
+    r3 = dict(rec)
+    r3["ratio"] = (1.0 + np.abs(rec["h"]) + np.float32(0.01)).astype(np.float32)
+    fa = np_(api.eval(M, dev(api, r2))[0])
+    fb = np_(api.eval(M, dev(api, r3))[0])
+    assert np.array_equal(fa, fb)
+
+
+def zipf_sorted(n, n_mat, seed):
+    g = np.random.default_rng(seed)
+    w = 1.0 / np.arange(1, n_mat + 1) ** 1.1
+    c = g.multinomial(n, w / w.sum())
+    c[g.choice(n_mat, 3, replace=False)] = 0   # empty materials
+    c[0] += n - c.sum()
+    return c
+
+
+def test_sorted_many_materials_and_plain_form(orc, api):
+    mats = I.materials(4)[:64]            # 64 tables exceed shared memory: sorted mode
+    counts = zipf_sorted(9001, 64, 5)
+    seg = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    rec = I.random_records(9001, n_mat=64, seed=44, wi_mode="cosine", sample=True)
+    rec["mat_id"] = (np.searchsorted(seg, np.arange(9001), side="right") - 1).astype(np.int32)
+    M, d, (f, p, st), *_ = check_eval(orc, api, mats, rec, seg=seg, name="c4")
+    # without seg_offsets the tables do not fit: a clean error
+    d2 = dict(d)
+    d2.pop("seg_offsets")
+    with pytest.raises(RuntimeError, match="seg_offsets"):
+        api.eval(M, d2)
+    # plain per-material form agrees with the persistent kernel
+    o = api.plain(0, M, d, seg)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(np_(o["f"]), f, rtol=1e-6, atol=1e-7)
+    assert np.array_equal(np_(o["status"]), st)
+    ws, w, ps, ls = api.sample(M, d)
+    o2 = api.plain(1, M, d, seg)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(np_(o2["weight"]), np_(w), rtol=1e-6, atol=1e-7)
+    assert np.array_equal(np_(o2["status"]), np_(ls))
+    # every launch shape gives the same answer
+    for block, items in ((128, 1), (512, 4)):
+        M.set_launch_config(0, block, items)
+        f2 = np_(api.eval(M, d)[0])
+        np.testing.assert_allclose(f2, f, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("sorted_mode", [False, True])
+def test_backward_matches_oracle_gradient(orc, api, sorted_mode):
+    mats = I.materials(5)[:12]
+    n = 6007
+    rec = I.random_records(n, n_mat=12, seed=51, wi_mode="cosine", sorted_ids=True, v_max=20.0)
+    rec["ratio"] = np.where(np.arange(n) % 3 == 0, 0.4, 0.0).astype(np.float32)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 12) if sorted_mode else None
+    g = np.random.default_rng(52).uniform(-1, 1, (3, n)).astype(np.float32)
+    # records on a branch have no unique derivative: give them no weight
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, rec)
+    good = PU.split_conditioned([fb], [(q[0],) for q in pert], sb, [q[2] for q in pert],
+                                frac=0.02)
+    g[:, ~good] = 0.0
+    grad_o, _, J = orc.grad_records(mats, rec, g.astype(np.float64), threads=8, jac=True)
+    scale = np.zeros((12, 8))
+    np.add.at(scale, rec["mat_id"], np.abs(g.T[:, :, None] * J).sum(1))
+    M = api.Materials(mats)
+    d = dev(api, rec, seg)
+    gt = torch.from_numpy(g).cuda()
+    grad_g = np_(api.eval_backward(M, d, gt))
+    err = np.abs(grad_g - grad_o)
+    assert (err <= 1e-4 * scale + 1e-6).all(), (err / (scale + 1e-12)).max()
+    if sorted_mode:
+        a = np_(api.eval_backward(M, d, gt, deterministic=True))
+        b = np_(api.eval_backward(M, d, gt, deterministic=True))
+        assert np.array_equal(a, b)
+        assert (np.abs(a - grad_o) <= 1e-4 * scale + 1e-6).all()
+    else:
+        with pytest.raises(RuntimeError, match="sorted"):
+            api.eval_backward(M, d, gt, deterministic=True)
+
+
+def test_autograd_function_and_fitting(orc, api):
+    mats = I.materials(5)[:4]
+    n = 4096
+    rec = I.random_records(n, n_mat=4, seed=61, wi_mode="cosine", sorted_ids=True, v_max=5.0)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 4)
+    M = api.Materials(mats)
+    d = dev(api, rec, seg)
+    theta_star = api.default_params(mats).cuda()
+    # target radiance from the oracle at the held-out parameters
+    tgt, _, st_t = orc.eval_records(mats, rec, threads=8)
+    target = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    mask = torch.from_numpy(st_t == 0).cuda()
+    g = torch.Generator().manual_seed(62)
+    theta = (theta_star.cpu() * (1 + 0.2 * (2 * torch.rand(theta_star.shape, generator=g) - 1)))
+    theta = theta.cuda()
+    theta[:, 5:7] = theta_star[:, 5:7]       # keep the twists (phase-sensitive)
+    theta.requires_grad_(True)
+    opt = torch.optim.Adam([theta], lr=0.01)
+    losses = []
+    for _ in range(60):
+        opt.zero_grad()
+        f, st = api.bysdf(theta, M, d)
+        loss = (((f - target) ** 2) * mask).sum() / n
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert losses[-1] < 0.3 * losses[0], losses[::10]
+    # backward through autograd equals the direct call
+    th = theta_star.clone().requires_grad_(True)
+    f, _ = api.bysdf(th, M, d)
+    gout = torch.randn_like(f)
+    f.backward(gout)
+    direct = api.eval_backward(M, d, gout.contiguous())
+    torch.testing.assert_close(th.grad, direct, rtol=1e-5, atol=1e-6)
+
+
+def test_edge_cases(orc, api):
+    mats = [I.material(n_plies=3)]
+    M = api.Materials(mats)
+    # n = 0 launches nothing and succeeds
+    empty = {k: v[..., :0] for k, v in I.random_records(4, seed=1).items()}
+    f, p, st = api.eval(M, dev(api, empty))
+    assert f.shape == (3, 0)
+    rec = I.random_records(40, seed=70, wi_mode="cosine", sample=True)
+    rec["h"][0] = np.nan                    # invalid inputs
+    rec["h"][1] = 1.5
+    rec["wi"][:, 2] = [0.0, 0.0, 2.0]
+    rec["mat_id"][3] = 7
+    rec["wo"][:, 4] = [0.0, 0.0, 0.0]
+    rec["h"][5], rec["h"][6] = 1.0, -1.0    # exact rims
+    rec["wi"][:, 7] = [0.0, 0.0, 1.0]       # along the yarn axis: no entry
+    rec["v"][8] = 1e5                       # far along the yarn
+    rec["u0"][9] = 1.0                      # random number out of range
+    d = dev(api, rec)
+    f, p, st = api.eval(M, d)
+    st = np_(st)
+    assert list(st[:5]) == [2, 2, 2, 2, 2] and st[7] == 1
+    fo, po, so = orc.eval_records(mats, rec)
+    assert np.array_equal(st[:9], so[:9])
+    for i in (5, 6, 8):
+        if so[i] == 0:
+            np.testing.assert_allclose(np_(f)[:, i], fo[:, i], rtol=1e-3, atol=1e-5)
+    wo, w, ps, ls = api.sample(M, d)
+    ls = np_(ls)
+    assert (ls[[0, 1, 2, 3, 9]] & 15 == 2).all()
+    assert ls[7] & 15 == 1
+    np.testing.assert_array_equal(np_(wo)[:, 7], -rec["wi"][:, 7])
+    # largest supported shapes
+    big = [I.material(n_plies=8, fibers_per_ply=4096, map_texels=1024, trace_iters=64, k_max=64)]
+    r = I.random_records(3001, seed=71, wi_mode="cosine", ratio="loguniform")
+    check_eval(orc, api, big, r, name="max-shapes", max_ill=0.05)
+
+
+def test_full_size_sampled_records(orc, api):
+    """Workload 2 at its full 2^24 records in the benchmark's fused launch:
+    spot-check 3000 sampled records against the oracle."""
+    cfg = 2
+    mats = I.materials(cfg)
+    rec = I.records(cfg)
+    M = api.Materials(mats)
+    d = dev(api, rec)
+    o = api.eval_sample_pdf(M, d)
+    torch.cuda.synchronize()
+    idx = I.sample_indices(cfg, 3000)
+    sub = {k: v[..., idx] for k, v in rec.items()}
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, sub)
+    good = PU.split_conditioned([fb, pb], [(q[0], q[1]) for q in pert], sb, [q[2] for q in pert])
+    f = np_(o["f"])[:, idx]
+    PU.assert_close_conditioned(f, fb, [q[0] for q in pert], good, "full.f")
+    PU.assert_close_conditioned(np_(o["pdf"])[idx], pb, [q[1] for q in pert], good, "full.pdf")
+    # property at full size: every record has a status and finite outputs
+    st = np_(o["status"])
+    assert set(np.unique(st)) <= {0, 1, 2, 3}
+    assert np.isfinite(np_(o["f"])).all() and np.isfinite(np_(o["weight"])).all()
+    assert (np_(o["f"]) >= 0).all() and (np_(o["pdf_s"]) >= 0).all()

@@ -142,26 +142,27 @@ def barrier():
 
 
 # ------------------------------------------------------------ CPU oracle --
-def cpu_oracle_rate(cfg: int, target_s: float = 8.0, max_records: int = 1 << 21):
+def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = 1 << 22):
     """The FP64 oracle, as it stands, on this host's cores: eval at omega_o
-    (with pdf) plus one sample per record, on a bounded prefix of the
-    workload sized to take about target_s."""
+    (with pdf) plus one sample per record, over a bounded prefix of the
+    workload, repeated until about target_s of CPU time has passed."""
     import oracle
     threads = os.cpu_count() or 1
     mats = I.materials(cfg)
-    n = 1 << 14
+    n = min(max_records, I.N_RECORDS[cfg])
+    rec = I.records(cfg, 0, n)
+    done, t0 = 0, time.perf_counter()
     while True:
-        rec = I.records(cfg, 0, n)
-        t0 = time.perf_counter()
         oracle.eval_records(mats, rec, threads=threads)
         oracle.sample_records(mats, rec, threads=threads)
+        done += n
         dt = time.perf_counter() - t0
-        if dt >= 0.5 * target_s or n >= max_records:
-            return dict(value=n / dt, unit=UNIT, cores=threads, kind="oracle",
-                        sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, "
-                               f"eval(+pdf) and one sample each, FP64, {threads} threads",
-                        seconds=dt, records=n)
-        n = min(max_records, int(n * min(16.0, max(2.0, target_s / max(dt, 1e-3)))))
+        if dt >= target_s:
+            break
+    return dict(value=done / dt, unit=UNIT, cores=threads, kind="oracle",
+                sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, eval(+pdf) and "
+                       f"one sample each, FP64, {threads} threads, {done // n} passes",
+                seconds=dt, records=done)
 
 
 def run_reference(args):
@@ -213,9 +214,9 @@ def timed(fn, steps, warmup, stream=None):
     return sum(per) / len(per), per
 
 
-def workload_device(api, cfg, rank):
+def workload_device(api, cfg, rank, count=0):
     seed = None if rank == 0 else I.SEED_BASE + cfg + 1000 * rank
-    rec = I.records(cfg, seed=seed)
+    rec = I.records(cfg, 0, count or None, seed=seed)
     seg = I.seg_offsets(cfg, seed=seed)
     d = api.records_to_device(rec, "cuda", seg)
     return rec, d, seg
@@ -236,12 +237,14 @@ def sorted_copy(d, n_mat):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads")
     ap.add_argument("--profile", action="store_true",
                     help="main workload only, no clocks/e2e/CPU baseline (for ncu)")
+    ap.add_argument("--records", type=int, default=0,
+                    help="use only the first N records of the main workload (profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -263,7 +266,7 @@ def main():
     cfg = MAIN_CFG
     mats = I.materials(cfg)
     M = api.Materials(mats)
-    rec, d, _ = workload_device(api, cfg, rank)
+    rec, d, _ = workload_device(api, cfg, rank, args.records)
     n = int(d["h"].shape[0])
     out = api.alloc_fused(n, "cuda")
     step = lambda: api.eval_sample_pdf(M, d, out=out)  # noqa: E731

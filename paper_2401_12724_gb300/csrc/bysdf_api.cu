@@ -329,6 +329,7 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   const bool need_wo = (bits & (OPF_EVAL | OPF_PDF)) != 0;
   int rc = check_hits(m, h, need_wo, n);
   if (rc) return rc;
+  if (n == 0) return BYSDF_OK;
   if (bits & OPF_EVAL) {
     if ((rc = check_out(o.f_rgb, "f_rgb"))) return rc;
   }
@@ -343,7 +344,6 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
         (rc = check_out(o.pdf_s, "pdf (sample)")) || (rc = check_out(o.lobe_status, "lobe_status")))
       return rc;
   }
-  if (n == 0) return BYSDF_OK;
   KArgs a;
   if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a))) return rc;
   if (!(bits & OPF_SAMPLE) || bits == (OPF_EVAL | OPF_SAMPLE)) a.wo = h->wo;
@@ -600,6 +600,7 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
     return fail(BYSDF_E_ARG, "bysdf_plain: op must be EVAL, SAMPLE or PDF");
   int rc = check_hits(m, hits, bits != OPF_SAMPLE, n);
   if (rc) return rc;
+  if (n == 0) return BYSDF_OK;
   if (!seg_offsets_host) return fail(BYSDF_E_ARG, "seg_offsets_host is NULL");
   if (seg_offsets_host[0] != 0 || seg_offsets_host[m->n_mat] != n)
     return fail(BYSDF_E_ARG, "seg_offsets_host must run from 0 to n");
@@ -614,7 +615,6 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
         (rc = check_out(weight, "weight")))
       return rc;
   }
-  if (n == 0) return BYSDF_OK;
   KArgs a;
   std::memset(&a, 0, sizeof(a));
   a.table = m->d_table;

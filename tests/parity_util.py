@@ -24,16 +24,21 @@ def tol(ref):
     return ABS + REL * np.abs(ref)
 
 
-def perturb(rec: dict, k: int, eps: float = 2.0 ** -20, sample: bool = False) -> dict:
+def perturb(rec: dict, k: int, eps: float = 2.0 ** -21, sample: bool = False) -> dict:
+    """A copy of the records moved by about the GPU path's own float32
+    rounding of its internal quantities: entry offset h, azimuth u and the
+    direction components by ~eps (absolute), the footprint ratio by eps
+    (relative), u0/u1 by eps/2.  The longitudinal position v is not moved:
+    the path forms its phases from v with compensated products, so its phase
+    error is far below what one ulp of v would cause."""
     g = np.random.default_rng(1000 + k)
     out = {kk: (vv.copy() if isinstance(vv, np.ndarray) else vv) for kk, vv in rec.items()}
     n = len(rec["h"])
 
     def r(*shape):
         return g.uniform(-1.0, 1.0, shape)
-    out["h"] = np.clip(rec["h"] * (1 + eps * r(n)), -1, 1).astype(np.float32)
-    out["u"] = (rec["u"] + eps * 6.3 * r(n)).astype(np.float32)
-    out["v"] = (rec["v"] * (1 + eps * r(n)) + eps * r(n)).astype(np.float32)
+    out["h"] = np.clip(rec["h"] + eps * r(n), -1, 1).astype(np.float32)
+    out["u"] = (rec["u"] + eps * r(n)).astype(np.float32)
     for key in ("wi", "wo"):
         if key in rec and rec[key] is not None:
             w = rec[key].astype(np.float64) + eps * r(3, n)
@@ -42,8 +47,18 @@ def perturb(rec: dict, k: int, eps: float = 2.0 ** -20, sample: bool = False) ->
         out["ratio"] = (rec["ratio"] * (1 + eps * r(n))).astype(np.float32)
     if sample:
         for key in ("u0", "u1"):
-            out[key] = np.clip(rec[key] + eps * r(n), 0.0, 1 - 2.0 ** -24).astype(np.float32)
+            out[key] = np.clip(rec[key] + 0.5 * eps * r(n), 0.0, 1 - 2.0 ** -24).astype(np.float32)
     return out
+
+
+def dump(name: str, **arrays):
+    """Save raw arrays for offline analysis when BYSDF_PARITY_DUMP is set."""
+    import os
+    d = os.environ.get("BYSDF_PARITY_DUMP")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        np.savez_compressed(os.path.join(d, name + ".npz"),
+                            **{k: np.asarray(v) for k, v in arrays.items()})
 
 
 def conditioning(orc_fn, rec: dict, n_pert: int = 6, sample: bool = False):

@@ -113,8 +113,12 @@ typedef struct bysdf_hits {
 typedef struct bysdf_launch_config {
   int32_t block;          /* threads per CTA: 128, 256 or 512               */
   int32_t items;          /* records per lane per warp tile: 1, 2 or 4       */
-  int32_t ctas_per_sm;    /* resident CTAs per SM the grid is sized for      */
-  int32_t reserved;
+  int32_t ctas_per_sm;    /* resident CTAs per SM the grid is sized for
+                             (0: as many as fit)                             */
+  int32_t occupancy;      /* register budget: 0 the default, 1 a tighter cap
+                             for more resident warps (forward: 16 vs 24
+                             warps per SM; backward: uncapped vs 16 warps;
+                             blocks of 128 or 256; spills go to L1)         */
 } bysdf_launch_config;
 
 enum { BYSDF_OP_EVAL = 0, BYSDF_OP_SAMPLE = 1, BYSDF_OP_PDF = 2, BYSDF_OP_FUSED = 3,
@@ -228,8 +232,10 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
                    void* workspace, size_t workspace_bytes, void* stream,
                    bysdf_launch_config* best);
 
-/* Device-side error word of a workspace (0 = none; bit 0: a bounded wait on
- * a shared-memory table copy gave up).  Synchronises the stream. */
+/* Device-side error word of a workspace, as left by the last call that used
+ * it (each call clears it first): 0 = none; bit 0: a bounded wait on a
+ * shared-memory table copy gave up; bit 1: a copy was still in flight after
+ * a second bounded wait.  Synchronises the stream. */
 int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err);
 
 #ifdef __cplusplus

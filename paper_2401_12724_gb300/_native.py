@@ -30,7 +30,7 @@ class Hits(C.Structure):
 
 class LaunchConfig(C.Structure):
     _fields_ = [("block", C.c_int32), ("items", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("occupancy", C.c_int32)]
 
 
 class Outputs(C.Structure):

@@ -94,14 +94,16 @@ class Materials:
         N.check(self.lib.bysdf_get_params(self.handle, _ptr(p), _stream(stream)), "bysdf_get_params")
         return p
 
-    def set_launch_config(self, op: int, block: int, items: int, ctas_per_sm: int = 0):
-        c = N.LaunchConfig(block, items, ctas_per_sm, 0)
+    def set_launch_config(self, op: int, block: int, items: int, ctas_per_sm: int = 0,
+                          occupancy: int = 0):
+        c = N.LaunchConfig(block, items, ctas_per_sm, occupancy)
         N.check(self.lib.bysdf_set_launch_config(self.handle, op, C.byref(c)), "set_launch_config")
 
     def launch_config(self, op: int) -> dict:
         c = N.LaunchConfig()
         N.check(self.lib.bysdf_get_launch_config(self.handle, op, C.byref(c)), "get_launch_config")
-        return dict(block=c.block, items=c.items, ctas_per_sm=c.ctas_per_sm)
+        return dict(block=c.block, items=c.items, ctas_per_sm=c.ctas_per_sm,
+                    occupancy=c.occupancy)
 
     def workspace_error(self, stream=None) -> int:
         err = C.c_uint32(0)
@@ -252,7 +254,8 @@ def autotune(mats: Materials, op: int, rec: dict, out: dict | None = None, grad_
         mats.handle, op, C.byref(hits_struct(rec, sample=samp)), _ptr(rec.get("u0")),
         _ptr(rec.get("u1")), _ptr(grad_f), n, C.byref(outs), _ptr(ws), ws.numel(),
         _stream(stream), C.byref(best)), "bysdf_autotune")
-    return dict(block=best.block, items=best.items, ctas_per_sm=best.ctas_per_sm)
+    return dict(block=best.block, items=best.items, ctas_per_sm=best.ctas_per_sm,
+                occupancy=best.occupancy)
 
 
 def default_params(descs) -> torch.Tensor:

@@ -196,8 +196,9 @@ __global__ void k_read_params(const uint8_t* table, int n_mat, int stride, float
   for (int k = 0; k < 8; ++k) params[i * 8 + k] = p[k];
 }
 
-// Tile plan: reset the tile counter; for material-sorted records also the
-// first warp tile of every material (exclusive scan of ceil(count / tile)).
+// Tile plan: reset the tile counter and the error word; for material-sorted
+// records also the first warp tile of every material (exclusive scan of
+// ceil(count / tile)).
 __global__ void __launch_bounds__(1024) k_plan(WsCtl* ctl, int32_t* tile_start,
                                                const int64_t* seg, int n_mat, int tile) {
   __shared__ int64_t part[1024];
@@ -226,7 +227,10 @@ __global__ void __launch_bounds__(1024) k_plan(WsCtl* ctl, int32_t* tile_start,
     }
     if (tid == 1023) tile_start[n_mat] = (int32_t)part[1023];
   }
-  if (tid == 0) ctl->tile_counter = 0;
+  if (tid == 0) {
+    ctl->tile_counter = 0;
+    ctl->err = 0u;
+  }
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -239,7 +243,7 @@ bysdf_launch_config default_cfg() {
   c.block = 256;
   c.items = 2;
   c.ctas_per_sm = 0;  // 0: as many as fit
-  c.reserved = 0;
+  c.occupancy = 0;
   return c;
 }
 
@@ -360,11 +364,11 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   const size_t smem = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
                                               : (size_t)(c.block / 32) * m->stride;
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
-  if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, smem));
+  if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, c.items, c.occupancy, smem));
   int occ = 0;
-  BY_CU(forward_occupancy(bits, c.block, smem, &occ));
+  BY_CU(forward_occupancy(bits, c.block, c.items, c.occupancy, smem, &occ));
   if ((rc = plan(m, a, ws, st))) return rc;
-  BY_CU(launch_forward(bits, a, c.block, grid_for(m, c, occ), smem, st));
+  BY_CU(launch_forward(bits, a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));
   return BYSDF_OK;
 }
 
@@ -391,12 +395,12 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
                           ? (size_t)m->n_mat * m->stride + sizeof(float) * 8 * m->n_mat
                           : (size_t)(c.block / 32) * m->stride;
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
-  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, smem));
+  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, c.occupancy, smem));
   int occ = 0;
-  BY_CU(backward_occupancy(c.block, smem, &occ));
+  BY_CU(backward_occupancy(c.block, c.occupancy, smem, &occ));
   if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * 8 * m->n_mat, st));
   if ((rc = plan(m, a, ws, st))) return rc;
-  BY_CU(launch_backward(a, c.block, grid_for(m, c, occ), smem, st));
+  BY_CU(launch_backward(a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));
   if (deterministic) BY_CU(launch_reduce_partials(a, st));
   return BYSDF_OK;
 }
@@ -647,8 +651,10 @@ int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_confi
   if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
   if (cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
     return fail(BYSDF_E_ARG, "block must be 128, 256 or 512");
-  if (cfg->items < 1 || cfg->items > 8) return fail(BYSDF_E_ARG, "items outside [1, 8]");
+  if (cfg->items != 1 && cfg->items != 2 && cfg->items != 4)
+    return fail(BYSDF_E_ARG, "items must be 1, 2 or 4");
   if (cfg->ctas_per_sm < 0) return fail(BYSDF_E_ARG, "ctas_per_sm < 0");
+  if (cfg->occupancy != 0 && cfg->occupancy != 1) return fail(BYSDF_E_ARG, "occupancy must be 0 or 1");
   m->cfg[op] = *cfg;
   return BYSDF_OK;
 }
@@ -681,8 +687,9 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
   int rc = BYSDF_OK;
   for (int block : {128, 256, 512}) {
     for (int items : {1, 2, 4}) {
-      for (int cps : {0, 1, 2}) {
-        bysdf_launch_config c{block, items, cps, 0};
+      for (int occ_mode : {0, 1}) {
+        if (occ_mode == 1 && block == 512) continue;
+        bysdf_launch_config c{block, items, 0, occ_mode};
         if ((rc = run(c))) break;  // warm-up (and validation)
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && rc == BYSDF_OK; ++r) rc = run(c);

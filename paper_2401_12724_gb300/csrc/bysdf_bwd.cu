@@ -7,8 +7,8 @@
 
 namespace bysdf {
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_backward(const KArgs a) {
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[BLOCK / 32];
   // MODE_ALL_SMEM: per-CTA accumulators behind the tables
@@ -92,29 +92,32 @@ __global__ void k_reduce_partials(const KArgs a) {
   }
 }
 
-static const void* bwd_fn(int block) {
+// occupancy 0: registers as needed (8 warps per SM at 256 threads);
+// occupancy 1: at most 128 registers (16 warps per SM; the rest spills).
+static const void* bwd_fn(int block, int occ) {
   switch (block) {
-    case 128: return (const void*)k_backward<128>;
-    case 256: return (const void*)k_backward<256>;
-    case 512: return (const void*)k_backward<512>;
+    case 128: return occ ? (const void*)k_backward<128, 4> : (const void*)k_backward<128, 1>;
+    case 256: return occ ? (const void*)k_backward<256, 2> : (const void*)k_backward<256, 1>;
+    case 512: return (const void*)k_backward<512, 1>;
   }
   return nullptr;
 }
 
-cudaError_t set_backward_smem_limit(int block, size_t smem) {
-  const void* f = bwd_fn(block);
+cudaError_t set_backward_smem_limit(int block, int occ, size_t smem) {
+  const void* f = bwd_fn(block, occ);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t backward_occupancy(int block, size_t smem, int* ctas) {
-  const void* f = bwd_fn(block);
+cudaError_t backward_occupancy(int block, int occ, size_t smem, int* ctas) {
+  const void* f = bwd_fn(block, occ);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block, smem);
 }
 
-cudaError_t launch_backward(const KArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
-  const void* f = bwd_fn(block);
+cudaError_t launch_backward(const KArgs& a, int block, int occ, int grid, size_t smem,
+                            cudaStream_t st) {
+  const void* f = bwd_fn(block, occ);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<KArgs*>(&a)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, st);

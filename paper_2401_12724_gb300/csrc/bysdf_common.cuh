@@ -37,9 +37,11 @@ __host__ __device__ inline size_t mat_stride_bytes(int t_max) {
   return sizeof(MatDev) + sizeof(float2) * (size_t)t_max;
 }
 
-// Differentiable parameter slots carried by the dual numbers of the backward
-// kernels (albedo is linear and handled in closed form).
-enum { D_BETA_T = 0, D_BETA_B = 1, D_ALPHA_P = 2, D_ALPHA_F = 3, D_SIGMA_S = 4, ND = 5 };
+// Parameter slots carried by the dual numbers of the backward kernel: the two
+// helix angles, which move the whole geometry.  Albedo (linear), shadow
+// density (only through G = exp(-sigma_s occlusion)) and roughness (only
+// through GGX D and Smith G1) are differentiated in closed form.
+enum { D_ALPHA_P = 0, D_ALPHA_F = 1, ND = 2 };
 
 // ------------------------------------------------------------ dual numbers --
 template <int N>

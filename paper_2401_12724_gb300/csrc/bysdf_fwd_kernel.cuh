@@ -1,0 +1,83 @@
+// The persistent forward kernel template (eval / sample / pdf / fused) and the
+// table of its instantiations; each op's instantiations compile in their own
+// translation unit (bysdf_fwd_<op>.cu).
+#pragma once
+
+#include "bysdf_launch.h"
+
+namespace bysdf {
+
+template <int OP, int BLOCK, int ITEMS, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bars[BLOCK / 32];
+  constexpr bool kWo = (OP & (OPF_EVAL | OPF_PDF)) != 0;
+  constexpr bool kU = (OP & OPF_SAMPLE) != 0;
+  persistent_loop<BLOCK>(a, smem, bars,
+                         [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane, int) {
+    uint32_t order[ITEMS];
+    tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, order);
+#pragma unroll 1
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t e = pick<ITEMS>(order, j);
+      if (e == 0xffffffffu) continue;
+      const int64_t i = begin + (e & 0xffu);
+      Record q;
+      load_record(a, i, kWo, kU, q);
+      const MatDev* m;
+      if (mat >= 0) {
+        q.mat = mat;
+        m = reinterpret_cast<const MatDev*>(slot);
+      } else {
+        q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
+        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
+      }
+      forward_record<OP>(a, *m, reinterpret_cast<const float2*>(m + 1), i, q);
+    }
+  });
+}
+
+// Register budget per launch shape: occupancy 0 caps registers so that 16
+// warps fit on an SM (128 per thread), occupancy 1 so that 24 fit (80 per
+// thread; the rest spills to L1).
+template <int BLOCK, int OCC>
+struct MinBlocks {
+  static constexpr int value = OCC == 1 ? (BLOCK == 128 ? 6 : (BLOCK == 256 ? 3 : 1))
+                                        : (BLOCK >= 512 ? 1 : 512 / BLOCK);
+};
+
+template <int OP, int BLOCK, int ITEMS>
+const void* fwd_kernel_bi(int occ) {
+  if (occ == 1 && BLOCK < 512)
+    return (const void*)k_forward<OP, BLOCK, ITEMS, MinBlocks<BLOCK, 1>::value>;
+  return (const void*)k_forward<OP, BLOCK, ITEMS, MinBlocks<BLOCK, 0>::value>;
+}
+
+template <int OP, int BLOCK>
+const void* fwd_kernel_b(int items, int occ) {
+  switch (items) {
+    case 1: return fwd_kernel_bi<OP, BLOCK, 1>(occ);
+    case 2: return fwd_kernel_bi<OP, BLOCK, 2>(occ);
+    case 4: return fwd_kernel_bi<OP, BLOCK, 4>(occ);
+  }
+  return nullptr;
+}
+
+template <int OP>
+const void* fwd_kernel(int block, int items, int occ) {
+  switch (block) {
+    case 128: return fwd_kernel_b<OP, 128>(items, occ);
+    case 256: return fwd_kernel_b<OP, 256>(items, occ);
+    case 512: return fwd_kernel_b<OP, 512>(items, occ);
+  }
+  return nullptr;
+}
+
+// one definition per op, in bysdf_fwd_<op>.cu
+const void* fwd_kernel_eval(int block, int items, int occ);
+const void* fwd_kernel_sample(int block, int items, int occ);
+const void* fwd_kernel_pdf(int block, int items, int occ);
+const void* fwd_kernel_fused(int block, int items, int occ);
+
+}  // namespace bysdf

@@ -212,18 +212,27 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   Shade<D> s;
   make_shade(m, mv, G, q, s);
   LobeVals<D> L;
-  eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L);
+  float dln_a[2] = {0.f, 0.f};
+  eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L, dln_a);
   const int64_t n = a.n;
   const float g0 = __ldg(a.grad_f + i), g1 = __ldg(a.grad_f + n + i),
               g2 = __ldg(a.grad_f + 2 * n + i);
-  // f_c = spec + albedo_c body: closed form in the albedo, duals elsewhere
+  // f_c = spec + albedo_c body
   const float gs = g0 + g1 + g2;
   const float gb = g0 * m.alb[0] + g1 * m.alb[1] + g2 * m.alb[2];
   gout[0] = g0 * L.body.v;
   gout[1] = g1 * L.body.v;
   gout[2] = g2 * L.body.v;
-#pragma unroll
-  for (int k = 0; k < ND; ++k) gout[3 + k] = gs * L.spec.d[k] + gb * L.body.d[k];
+  // roughness: d spec / d beta = spec * d ln spec / d alpha (alpha = beta +
+  // footprint term, unless clamped)
+  gout[3] = s.at_free ? gs * L.spec.v * dln_a[0] : 0.f;
+  gout[4] = s.ab_free ? gs * L.spec.v * dln_a[1] : 0.f;
+  // helix angles: the dual tangents
+  gout[5] = gs * L.spec.d[D_ALPHA_P] + gb * L.body.d[D_ALPHA_P];
+  gout[6] = gs * L.spec.d[D_ALPHA_F] + gb * L.body.d[D_ALPHA_F];
+  // shadow density: the body lobes are proportional to G
+  const float Gv = G.g.v;
+  gout[7] = Gv > 0.f ? gb * L.body.v * (G.dg_dsig / Gv) : 0.f;
 }
 
 // Shared-memory staging of the material tables and the warp tile loop, common
@@ -304,6 +313,83 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
     }
     body(begin, end, mat, slot, lane, tile);
   }
+}
+
+// ---------------------------------------------------- work order in a tile --
+// Lanes of a warp run in lock step, so a round costs as much as its most
+// expensive record (most plies, most footprint nodes).  The records of a warp
+// tile are therefore taken in order of an estimated cost, K nodes x N_p
+// plies, then of material (so that the lanes of a round mostly read one
+// table), by a bitonic sort of (cost << 16 | material << 8 | index) keys
+// across the warp (ITEMS keys per lane; element e = j * 32 + lane lives in
+// v[j] of lane `lane`).  Empty slots hold 0xffffffff and sort last.
+template <int ITEMS>
+__device__ __forceinline__ void warp_bitonic_sort(uint32_t (&v)[ITEMS], int lane) {
+  constexpr int N = 32 * ITEMS;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int s = k >> 1; s > 0; s >>= 1) {
+      if (s < 32) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+          const int e = j * 32 + lane;
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[j], s);
+          const bool up = (e & k) == 0;
+          const bool lower = (e & s) == 0;
+          v[j] = (lower == up) ? min(v[j], o) : max(v[j], o);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+          const int jj = j ^ (s >> 5);
+          if (jj > j) {
+            const bool up = ((j * 32 + lane) & k) == 0;
+            const uint32_t x = v[j], y = v[jj];
+            v[j] = up ? min(x, y) : max(x, y);
+            v[jj] = up ? max(x, y) : min(x, y);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, int64_t begin,
+                                           int64_t end, int mat, const uint8_t* slot, int lane,
+                                           uint32_t (&v)[ITEMS]) {
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int idx = j * 32 + lane;
+    const int64_t i = begin + idx;
+    v[j] = 0xffffffffu;
+    if (i < end) {
+      const MatDev* m;
+      int mm = 0;
+      if (mat >= 0) {
+        m = reinterpret_cast<const MatDev*>(slot);
+      } else {
+        mm = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        mm = (mm >= 0 && mm < a.n_mat) ? mm : 0;
+        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
+      }
+      int K = 1;
+      if (a.ratio) K = footprint(__ldg(a.h + i), __ldg(a.ratio + i), m->kmax).K;
+      const uint32_t cost = (uint32_t)min(K * m->np, 32767);
+      v[j] = (cost << 16) | ((uint32_t)(mm & 0xff) << 8) | (uint32_t)idx;
+    }
+  }
+  warp_bitonic_sort<ITEMS>(v, lane);
+}
+
+template <int ITEMS>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[ITEMS], int j) {
+  uint32_t e = v[0];
+#pragma unroll
+  for (int jj = 1; jj < ITEMS; ++jj)
+    if (jj == j) e = v[jj];
+  return e;
 }
 
 }  // namespace bysdf

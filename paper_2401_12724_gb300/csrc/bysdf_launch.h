@@ -8,15 +8,16 @@
 namespace bysdf {
 
 // op: OPF_* bit set (EVAL, SAMPLE, PDF, EVAL|SAMPLE).  Returns the launch error.
-cudaError_t launch_forward(int op, const KArgs& a, int block, int grid, size_t smem,
+cudaError_t launch_forward(int op, const KArgs& a, int block, int occ, int grid, size_t smem,
                            cudaStream_t st);
 cudaError_t launch_plain(int op, const KArgs& a, int mat, int64_t begin, int64_t end,
                          cudaStream_t st);
-cudaError_t launch_backward(const KArgs& a, int block, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_backward(const KArgs& a, int block, int occ, int grid, size_t smem,
+                            cudaStream_t st);
 cudaError_t launch_reduce_partials(const KArgs& a, cudaStream_t st);
-cudaError_t set_forward_smem_limit(int op, int block, size_t smem);
-cudaError_t set_backward_smem_limit(int block, size_t smem);
-cudaError_t forward_occupancy(int op, int block, size_t smem, int* ctas);
-cudaError_t backward_occupancy(int block, size_t smem, int* ctas);
+cudaError_t set_forward_smem_limit(int op, int block, int items, int occ, size_t smem);
+cudaError_t set_backward_smem_limit(int block, int occ, size_t smem);
+cudaError_t forward_occupancy(int op, int block, int items, int occ, size_t smem, int* ctas);
+cudaError_t backward_occupancy(int block, int occ, size_t smem, int* ctas);
 
 }  // namespace bysdf

@@ -60,9 +60,6 @@ __device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m) {
     q.kf.d[D_ALPHA_F] = m.dkf;
     q.cos_af.d[D_ALPHA_F] = -m.sin_af;
     q.sin_af.d[D_ALPHA_F] = m.cos_af;
-    q.sigma_s.d[D_SIGMA_S] = 1.f;
-    q.beta_t.d[D_BETA_T] = 1.f;
-    q.beta_b.d[D_BETA_B] = 1.f;
   }
   return q;
 }
@@ -131,8 +128,10 @@ template <class S>
 struct NodeGeo {
   bool hit;
   int ni;
+  int ply;  // closest ply
   V3<S> x, nf, tf;
-  S g;  // G_p * G_f
+  S g;            // G_p * G_f
+  float dg_dsig;  // d(G_p G_f) / d sigma_s (value)
 };
 
 // Sec. 3.5.1: periodic linear interpolation of the tabulated maps; w is the
@@ -159,22 +158,36 @@ template <class S>
 __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
                                               const MatVars<S>& mv, float X0x, float X0y,
                                               float ex, float ey, float v, float kappa,
-                                              float wx, float wy, const S& turns_v,
-                                              const S& phase_f_v, NodeGeo<S>& out) {
+                                              float wx, float wy, const S& s0v,
+                                              const S& c0v, const S& phase_f_v,
+                                              NodeGeo<S>& out, int only_ply = -1,
+                                              int ni_known = 0) {
   const float Rp = m.Rp, Rc = m.Rc;
   out.hit = false;
   out.ni = 0;
   int best = -1;
   S best_t = S(0.f), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
-  for (int k = 0; k < m.np; ++k) {
+  // only_ply >= 0: the closest ply and N_i are known already (from a float
+  // pass over all plies); trace that ply alone
+  const int k_lo = only_ply >= 0 ? only_ply : 0;
+  const int k_hi = only_ply >= 0 ? only_ply + 1 : m.np;
+  for (int k = k_lo; k < k_hi; ++k) {
+    // phase of ply k in the cross-section at the yarn hit: ply 0's phase
+    // turned by 2 pi k / N_p
+    const float rc = m.rot_c[k], rs = m.rot_s[k];
+    const S ck = c0v * rc - s0v * rs, sk = s0v * rc + c0v * rs;
     // cross-section update: ply centre at the height of the current
     // intersection, 2D ray / circle intersection there, repeat
-    const S turns0 = turns_v + (float)k * m.inv_np;
-    S t = S(0.f), cx = S(0.f), cy = S(0.f), sp = S(0.f), cp = S(1.f);
+    S t = S(0.f), cx = S(0.f), cy = S(0.f), sp = sk, cp = ck;
     bool hit = true;
     for (int n = 0; n < m.nit; ++n) {
-      const S turns = turns0 + mv.kp * (kappa * t);
-      xsincos_turns(turns, &sp, &cp);
+      if (n > 0) {
+        // the helix phase advances by 2 pi kp dz with dz = kappa t
+        S sd, cd;
+        xsincos_turns(mv.kp * (kappa * t), &sd, &cd);
+        cp = ck * cd - sk * sd;
+        sp = sk * cd + ck * sd;
+      }
       cx = Rc * cp;
       cy = Rc * sp;
       const S qx = X0x - cx, qy = X0y - cy;
@@ -185,12 +198,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
         hit = false;
         break;
       }
-      const S tn = xmax0(-b - xsqrt(disc));
-      if constexpr (!is_dual<S>::value) {
-        // a repeated iterate is a fixed point: every further update returns it
-        if (tn == t) break;
-      }
-      t = tn;
+      t = xmax0(-b - xsqrt(disc));
     }
     if (!hit) continue;
     out.ni += 1;
@@ -204,7 +212,9 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     }
   }
   if (best < 0) return;
+  if (only_ply >= 0) out.ni = ni_known;
   out.hit = true;
+  out.ply = best;
   // Sec. 3.4: hit point, ply normal (from the ply centre, in the circular
   // cross-section), ply tangent (derivative of the helix through x)
   const S xx = X0x + best_t * ex, xy = X0y + best_t * ey;
@@ -245,7 +255,9 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
       if (vf(s2) > 0.f) occ = occ + (s2 - xmax0(-b - sq));
     }
   }
-  out.g = xexp(-(mv.sigma_s * (occ * m.inv_2Rp + of)));
+  const S occ_all = occ * m.inv_2Rp + of;
+  out.g = xexp(-(mv.sigma_s * occ_all));
+  out.dg_dsig = -vf(occ_all) * vf(out.g);
 }
 
 // Aggregated geometry of a record (Sec. 4.2 Eqs. 8-11, W = 1).
@@ -255,6 +267,7 @@ struct Geo {
   float width;
   V3<S> n, t, x;
   S g, ni;
+  float dg_dsig;
 };
 
 template <class S>
@@ -274,10 +287,24 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
   const float inv_l = 1.0f / lxy;
   const float kappa = -q.wi[2] * inv_l;
   const float wx = q.wi[0] * inv_l, wy = q.wi[1] * inv_l;
+  // ply 0's phase at the hit's cross-section, and the fiber phase there
   const S turns_v = frac_prod_s(mv.kp, m.kp_hi, m.kp_lo, q.v);
+  S s0v, c0v;
+  xsincos_turns(turns_v, &s0v, &c0v);
   const S phase_f_v = frac_prod_s(mv.kf, m.kf_hi, m.kf_lo, q.v);
+  // derivatives follow the branch the values take: a float pass picks the
+  // closest ply and N_i of each node, the dual pass re-traces that ply only
+  MatVars<float> mvf;
+  float s0f = 0.f, c0f = 1.f, pff = 0.f;
+  if constexpr (is_dual<S>::value) {
+    mvf = mat_vars<float>(m);
+    s0f = s0v.v;
+    c0f = c0v.v;
+    pff = phase_f_v.v;
+  }
   V3<S> ns = lift3<S>(0.f, 0.f, 0.f), ts = ns, xs = ns;
   S gs = S(0.f);
+  float dgs = 0.f;
   int nis = 0, nhit = 0;
   const bool near = fp.K == 1 && fp.width == 0.0f;
   for (int j = 0; j < fp.K; ++j) {
@@ -291,7 +318,15 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
     X0x *= m.R;
     X0y *= m.R;
     NodeGeo<S> nd;
-    node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, turns_v, phase_f_v, nd);
+    if constexpr (is_dual<S>::value) {
+      NodeGeo<float> pick;
+      node_geometry(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick);
+      if (!pick.hit) continue;
+      node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd,
+                    pick.ply, pick.ni);
+    } else {
+      node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd);
+    }
     if (!nd.hit) continue;
     nhit += 1;
     nis += nd.ni;
@@ -299,6 +334,7 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
     ts = ts + nd.tf;
     xs = xs + nd.x;
     gs = gs + nd.g;
+    dgs += nd.dg_dsig;
   }
   if (nhit == 0) return;
   const float inv = 1.0f / (float)nhit;
@@ -311,6 +347,7 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
   G.t = tperp * (S(1.f) / tl);
   G.x = xs * inv;
   G.g = gs * inv;
+  G.dg_dsig = dgs * inv;
   G.ni = S((float)nis * inv);
   G.status = ST_OK;
 }
@@ -375,6 +412,9 @@ template <class S>
 struct Shade {
   V3<S> t, b, n, wi;
   S mui, at, ab, g, fr;
+  bool at_free, ab_free;  // roughness not clamped (its derivative passes)
+  S body_x0;  // r B G / (1 + a(mu_i)): f_x^B per unit albedo before its angular term
+  S body_y0;  // (1 - r) B G / pi: f_y^B per unit albedo per unit cosine
   // transmission path (f_y^S)
   bool tt_ok;
   V3<S> iy, by, ny;
@@ -405,8 +445,18 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   const float hw = 0.5f * G.width;
   s.at = clamp_alpha(mv.beta_t + hw);
   s.ab = clamp_alpha(mv.beta_b + hw);
+  s.at_free = vf(s.at) == vf(mv.beta_t + hw);
+  s.ab_free = vf(s.ab) == vf(mv.beta_b + hw);
   s.g = G.g;
   s.fr = fresnel(s.mui, m.eta);
+  // Eq. 5: the Lommel-Seeliger + Lambert bracket divided by its albedo
+  // 1 + a(mu_i), a(mu) = (1 - mu ln(1 + 1/mu)) / 2; Eq. 6: Lambert
+  s.body_x0 = S(0.f);
+  if (vf(s.mui) > 0.f) {
+    const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + S(1.f) / s.mui));
+    s.body_x0 = (m.r * m.B) * s.g / (1.0f + aLS);
+  }
+  s.body_y0 = ((1.0f - m.r) * m.B * (1.0f / kPi)) * s.g;
   s.tt_ok = false;
   // Sec. 4.1.1 (reading): smooth refraction into the yarn at x, straight path
   // to the yarn surface y, attenuation tau^{N_i} (Eq. 4)
@@ -438,8 +488,29 @@ struct LobeVals {
 };
 
 template <class S>
+__device__ __forceinline__ V3<S> vsel(bool c, const V3<S>& a, const V3<S>& b) {
+  return c ? a : b;
+}
+
+// Closed-form d ln / d alpha of GGX D and Smith G1 (local frames, values).
+__device__ __forceinline__ void dln_ggx_d(float hx, float hy, float hz, float at, float ab,
+                                          float* dt, float* db) {
+  const float q = hx * hx / (at * at) + hy * hy / (ab * ab) + hz * hz;
+  *dt = -1.0f / at + 4.0f * hx * hx / (at * at * at * q);
+  *db = -1.0f / ab + 4.0f * hy * hy / (ab * ab * ab * q);
+}
+__device__ __forceinline__ void dln_ggx_g1(float wx, float wy, float wz, float at, float ab,
+                                           float* dt, float* db) {
+  const float an = fabsf(wz);
+  const float r = sqrtf(an * an + at * at * wx * wx + ab * ab * wy * wy);
+  const float k = 1.0f / (r * (an + r));
+  *dt = -at * wx * wx * k;
+  *db = -ab * wy * wy * k;
+}
+
+template <class S>
 __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, const V3<S>& wo,
-                                           LobeVals<S>& L) {
+                                           LobeVals<S>& L, float* dln_alpha = nullptr) {
   L.spec = S(0.f);
   L.body = S(0.f);
   L.pR = S(0.f);
@@ -448,53 +519,63 @@ __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, c
   L.pyb = S(0.f);
   if (!(vf(s.mui) > 0.f)) return;
   const S muo = dot(wo, s.n);
-  if (vf(muo) > 0.f) {
-    // Eq. 2, reflection (Walter et al. 2007 with GGX)
-    const V3<S> h = normalize(s.wi + wo);
-    const S wih = dot(s.wi, h), woh = dot(wo, h);
-    const V3<S> hl = to_local(h, s.t, s.b, s.n);
-    const V3<S> il = to_local(s.wi, s.t, s.b, s.n);
-    const V3<S> ol = to_local(wo, s.t, s.b, s.n);
-    const S D = ggx_d(hl, s.at, s.ab);
-    const S g1i = ggx_g1(il, wih, s.at, s.ab);
-    const S g1o = ggx_g1(ol, woh, s.at, s.ab);
-    const S F = fresnel(wih, m.eta);
+  const bool refl = vf(muo) > 0.f;
+  if (!refl && !(vf(muo) < 0.f)) return;
+  // Eqs. 5-6: body lobes, per unit albedo
+  if (refl) {
+    L.body = s.body_x0 * (S(1.0f / (4.0f * kPi)) / (s.mui + muo) + 1.0f / kPi) * muo;
+    L.pxb = muo * (1.0f / kPi);
+  } else {
+    L.body = s.body_y0 * (-muo);
+    L.pyb = -muo * (1.0f / kPi);
+  }
+  // Eq. 2 (reflection at x, Walter et al. 2007 with GGX) and Eq. 3 (exit BTDF
+  // at y from inside (eta) to outside (1), times the entry transmittance and
+  // tau^{N_i}) share one microfacet evaluation: GGX D at the half vector,
+  // Smith G1 of both directions, Fresnel -- in the frame of the lobe that
+  // applies to this omega_o
+  S ion = S(0.f);
+  if (!refl) {
+    if (!s.tt_ok) return;
+    ion = dot(s.iy, s.ny);
+    const S oon = dot(wo, s.ny);
+    if (!(vf(ion) < 0.f && vf(oon) > 0.f)) return;
+  }
+  const V3<S> fz = lift3<S>(0.f, 0.f, 1.f);
+  const V3<S> fn = vsel(refl, s.n, s.ny);
+  const V3<S> ft = vsel(refl, s.t, fz);
+  const V3<S> fb = vsel(refl, s.b, s.by);
+  const V3<S> vi = vsel(refl, s.wi, s.iy);
+  V3<S> h = normalize(refl ? s.wi + wo : -(s.iy * m.eta + wo));
+  if (vf(dot(h, fn)) < 0.f) h = -h;
+  const S ih = dot(vi, h), oh = dot(wo, h);
+  if (!refl && !(vf(ih) < 0.f && vf(oh) > 0.f)) return;
+  const V3<S> hl = to_local(h, ft, fb, fn), il = to_local(vi, ft, fb, fn),
+              ol = to_local(wo, ft, fb, fn);
+  const S D = ggx_d(hl, s.at, s.ab);
+  const S g1i = ggx_g1(il, ih, s.at, s.ab);
+  const S g1o = ggx_g1(ol, oh, s.at, s.ab);
+  if (dln_alpha) {
+    // the specular value is a product with D, G1(i), G1(o): its log
+    // derivative in the roughness is the sum of theirs
+    const float at = vf(s.at), ab = vf(s.ab);
+    float a0, a1, b0, b1, c0, c1;
+    dln_ggx_d(vf(hl.x), vf(hl.y), vf(hl.z), at, ab, &a0, &a1);
+    dln_ggx_g1(vf(il.x), vf(il.y), vf(il.z), at, ab, &b0, &b1);
+    dln_ggx_g1(vf(ol.x), vf(ol.y), vf(ol.z), at, ab, &c0, &c1);
+    dln_alpha[0] = a0 + b0 + c0;
+    dln_alpha[1] = a1 + b1 + c1;
+  }
+  const S F = fresnel(refl ? ih : -ih, refl ? m.eta : m.inv_eta);
+  if (refl) {
     const S q = g1i * D / (4.0f * s.mui);
     L.spec = m.ks * F * g1o * q;
     L.pR = q;
-    // Eq. 5 with LS = 1 / (4 pi (mu_i + mu_o)), normalised to albedo r B G
-    const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + S(1.f) / s.mui));
-    const S br = (S(1.0f / (4.0f * kPi)) / (s.mui + muo) + 1.0f / kPi) / (1.0f + aLS);
-    L.body = m.r * m.B * s.g * br * muo;
-    L.pxb = muo * (1.0f / kPi);
-  } else if (vf(muo) < 0.f) {
-    // Eq. 6, forward body
-    L.body = (1.0f - m.r) * m.B * s.g * (1.0f / kPi) * (-muo);
-    L.pyb = -muo * (1.0f / kPi);
-    // Eq. 3: exit BTDF at y from inside (eta) to outside (1), times the entry
-    // transmittance and tau^{N_i}
-    if (s.tt_ok) {
-      const S ion = dot(s.iy, s.ny), oon = dot(wo, s.ny);
-      if (vf(ion) < 0.f && vf(oon) > 0.f) {
-        V3<S> ht = normalize(-(s.iy * m.eta + wo));
-        if (vf(dot(ht, s.ny)) < 0.f) ht = -ht;
-        const S ih = dot(s.iy, ht), oh = dot(wo, ht);
-        if (vf(ih) < 0.f && vf(oh) > 0.f) {
-          const S den = m.eta * ih + oh;
-          const V3<S> z = lift3<S>(0.f, 0.f, 1.f);
-          const V3<S> hl = to_local(ht, z, s.by, s.ny);
-          const V3<S> il = to_local(s.iy, z, s.by, s.ny);
-          const V3<S> ol = to_local(wo, z, s.by, s.ny);
-          const S D = ggx_d(hl, s.at, s.ab);
-          const S g1i = ggx_g1(il, ih, s.at, s.ab);
-          const S g1o = ggx_g1(ol, oh, s.at, s.ab);
-          const S Fy = fresnel(-ih, m.inv_eta);
-          const S q = g1i * (-ih) * D * oh / ((-ion) * den * den);
-          L.spec = m.ks * s.tx * s.tau * (1.0f - Fy) * g1o * q;
-          L.pT = q;
-        }
-      }
-    }
+  } else {
+    const S den = m.eta * ih + oh;
+    const S q = g1i * (-ih) * D * oh / ((-ion) * den * den);
+    L.spec = m.ks * s.tx * s.tau * (1.0f - F) * g1o * q;
+    L.pT = q;
   }
 }
 
@@ -524,22 +605,22 @@ __device__ __forceinline__ bool sample_dir(const MatDev& m, const Shade<float>& 
   *lobe = k;
   float ur = P[k] > 0.f ? (u0 - lo) / P[k] : 0.f;
   ur = fminf(fmaxf(ur, 0.0f), 0.99999994f);
-  if (k == 0) {
-    const V3<float> il = to_local(s.wi, s.t, s.b, s.n);
-    const V3<float> ml = vndf_sample(il, s.at, s.ab, ur, u1);
-    const V3<float> mw = s.t * ml.x + s.b * ml.y + s.n * ml.z;
-    *wo = mw * (2.0f * dot(s.wi, mw)) - s.wi;
-    return dot(*wo, s.n) > 0.f;
-  }
-  if (k == 1) {
-    if (!s.tt_ok) return false;
-    const V3<float> Nn = -s.ny;
-    const V3<float> Tn = mk3<float>(0.f, 0.f, 1.f);
-    const V3<float> Bn = cross(Nn, Tn);
-    const V3<float> il = to_local(s.iy, Tn, Bn, Nn);
-    const V3<float> ml = vndf_sample(il, s.at, s.ab, ur, u1);
-    const V3<float> mw = Tn * ml.x + Bn * ml.y + Nn * ml.z;
-    const float c = dot(s.iy, mw);
+  if (k <= 1) {
+    // GGX visible normals (Heitz 2018): about n at x for reflection, about
+    // the inner normal at y for transmission -- one sampler, frame per lane
+    const bool refl = k == 0;
+    if (!refl && !s.tt_ok) return false;
+    const V3<float> N = refl ? s.n : -s.ny;
+    const V3<float> T = refl ? s.t : mk3<float>(0.f, 0.f, 1.f);
+    const V3<float> B = refl ? s.b : cross(N, T);
+    const V3<float> view = refl ? s.wi : s.iy;
+    const V3<float> ml = vndf_sample(to_local(view, T, B, N), s.at, s.ab, ur, u1);
+    const V3<float> mw = T * ml.x + B * ml.y + N * ml.z;
+    const float c = dot(view, mw);
+    if (refl) {
+      *wo = mw * (2.0f * c) - s.wi;
+      return dot(*wo, s.n) > 0.f;
+    }
     const float s2t = m.eta * m.eta * (1.0f - c * c);
     if (!(c > 0.f) || !(s2t < 1.0f)) return false;
     *wo = normalize(s.iy * (-m.eta) + mw * (m.eta * c - sqrtf(1.0f - s2t)));

@@ -232,6 +232,27 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
                    void* workspace, size_t workspace_bytes, void* stream,
                    bysdf_launch_config* best);
 
+/* Eval without a caller-provided workspace: the same computation and
+ * outputs as bysdf_eval, for callers that are not allowed to allocate device
+ * memory (for example a renderer plug-in whose host application owns every
+ * allocation, or code running where an allocation could synchronise the
+ * device or fail).  The paper has no counterpart; this is a library-level
+ * convenience.
+ *
+ * Scratch: a fixed array of BYSDF_NOALLOC_SCRATCH_BYTES in device memory,
+ * defined in the library, which every GPU that loads the library holds until
+ * the process exits.  It fits the tables of up to
+ * (BYSDF_NOALLOC_SCRATCH_BYTES - 256) / 4 - 1 = 4031 materials; larger tables
+ * return BYSDF_E_WORKSPACE.  The call allocates nothing.  Its first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array and clears the part that must
+ * start at zero; calls that may overlap on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller. */
+#define BYSDF_NOALLOC_SCRATCH_BYTES 16384
+int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                       float* f_rgb, float* pdf, uint8_t* status, void* stream);
+
 /* Device-side error word of a workspace, as left by the last call that used
  * it (each call clears it first): 0 = none; bit 0: a bounded wait on a
  * shared-memory table copy gave up; bit 1: a copy was still in flight after

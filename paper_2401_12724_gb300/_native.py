@@ -62,6 +62,7 @@ SYMBOLS = [
     ("bysdf_autotune", C.c_int, [P, C.c_int, C.POINTER(Hits), P, P, P, C.c_int64,
                                  C.POINTER(Outputs), P, C.c_size_t, P, C.POINTER(LaunchConfig)]),
     ("bysdf_workspace_error", C.c_int, [P, P, C.POINTER(C.c_uint32)]),
+    ("bysdf_eval_noalloc", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, P, P]),
 ]
 
 OP_EVAL, OP_SAMPLE, OP_PDF, OP_FUSED, OP_BACKWARD = range(5)

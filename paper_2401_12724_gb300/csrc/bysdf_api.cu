@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -270,7 +271,7 @@ int check_out(const void* p, const char* name) {
 
 // Common preparation of a persistent launch.
 int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, size_t ws_bytes,
-            int block, int items, KArgs* a) {
+            int block, int items, KArgs* a, size_t ws_need) {
   std::memset(a, 0, sizeof(*a));
   a->table = m->d_table;
   a->n_mat = m->n_mat;
@@ -296,7 +297,7 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
   a->n_tiles = (n + a->tile - 1) / a->tile;
   if (!ws) return fail(BYSDF_E_WORKSPACE, "workspace is NULL");
   if (!aligned16(ws)) return fail(BYSDF_E_ARG, "workspace not 16-byte aligned");
-  if (ws_bytes < bysdf_workspace_size(m, n))
+  if (ws_bytes < ws_need)
     return fail(BYSDF_E_WORKSPACE, "workspace smaller than bysdf_workspace_size()");
   a->ctl = reinterpret_cast<WsCtl*>(ws);
   a->tile_start = reinterpret_cast<const int32_t*>((uint8_t*)ws + ws_tile_start_off());
@@ -328,7 +329,7 @@ int op_bits(int op) {
 
 int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const float* u0,
                 const float* u1, int64_t n, const bysdf_outputs& o, void* ws, size_t ws_bytes,
-                cudaStream_t st, const bysdf_launch_config& c) {
+                cudaStream_t st, const bysdf_launch_config& c, size_t ws_need = 0) {
   const int bits = op_bits(op);
   const bool need_wo = (bits & (OPF_EVAL | OPF_PDF)) != 0;
   int rc = check_hits(m, h, need_wo, n);
@@ -349,7 +350,9 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
       return rc;
   }
   KArgs a;
-  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a))) return rc;
+  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a,
+                    ws_need ? ws_need : bysdf_workspace_size(m, n))))
+    return rc;
   if (!(bits & OPF_SAMPLE) || bits == (OPF_EVAL | OPF_SAMPLE)) a.wo = h->wo;
   if (bits == OPF_SAMPLE) a.wo = nullptr;
   a.u0 = u0;
@@ -386,7 +389,8 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
     return BYSDF_OK;
   }
   KArgs a;
-  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a))) return rc;
+  if ((rc = prepare(m, h, n, ws, ws_bytes, c.block, c.items, &a, bysdf_workspace_size(m, n))))
+    return rc;
   a.grad_f = grad_f;
   a.grad_params = grad_params;
   a.partials = deterministic ? reinterpret_cast<float*>((uint8_t*)ws + ws_partials_off(m->n_mat))
@@ -405,6 +409,35 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
   return BYSDF_OK;
 }
 
+}  // namespace
+
+// Scratch of bysdf_eval_noalloc: one fixed array per device that loads the
+// library (kept until the process exits).  Host code must not use its name
+// as an address: the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[BYSDF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  BY_CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(BYSDF_E_UNSUPPORTED, "device ordinal too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(BYSDF_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return BYSDF_OK;
+}
 }  // namespace
 
 // =================================================================== C ABI ==
@@ -543,6 +576,31 @@ int bysdf_eval(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, floa
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
                      reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_EVAL]);
+}
+
+int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                       float* f_rgb, float* pdf, uint8_t* status, void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  // the forward kernels need the control words and one first-tile entry per
+  // material; no per-record scratch
+  const size_t need = ws_partials_off(m->n_mat);
+  if (need > BYSDF_NOALLOC_SCRATCH_BYTES)
+    return fail(BYSDF_E_WORKSPACE, "bysdf_eval_noalloc: more materials than its fixed scratch "
+                                   "holds (at most 4031)");
+  int rc = check_hits(m, hits, true, n);
+  if (rc) return rc;
+  if (n == 0) return BYSDF_OK;
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the previous call's contents stay in the array: zero the control words
+  BY_CU(cudaMemsetAsync(scratch, 0, kWsCtl, st));
+  bysdf_outputs o{};
+  o.f_rgb = f_rgb;
+  o.pdf = pdf;
+  o.status = status;
+  return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, scratch,
+                     BYSDF_NOALLOC_SCRATCH_BYTES, st, m->cfg[BYSDF_OP_EVAL], need);
 }
 
 int bysdf_sample(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,

@@ -17,6 +17,7 @@ roofline of the fused kernel, and the FP64 oracle on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -47,9 +48,29 @@ OPS = {
     4: dict(eval=(541.0, 75.0), fused=(720.8, 94.6)),
     5: dict(eval=(397.7, 54.2)),
 }
+# DRAM traffic of the fused kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on the first 2^22 records of the
+# workload, per record; the records stream through once, so traffic scales
+# with the record count).  It is reported only while the kernel sources are
+# the ones captured (SHA-256 over csrc/ and include/bysdf.h).
+TRAFFIC_CAPTURE = dict(sources_sha256=None, bytes_per_record=None,
+                       summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM
 SM_MAX_MHZ = 2070.0
+
+
+def sources_sha256() -> str:
+    """Digest of the CUDA sources and the C header (file names and bytes)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2401_12724_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
+                   if f.endswith((".cu", ".cuh", ".h")))
+    for path in files + [os.path.join(ROOT, "include", "bysdf.h")]:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def peaks(sm_count: int, mhz: float):
@@ -313,7 +334,14 @@ def main():
     else:
         roof = dict(bound="alu", pipe="xu", achieved=ach_xu, peak=pk["xu_tops"], unit="Top/s",
                     frac=frac_xu)
-    roof.update(traffic=None, peak_basis=f"{sm_count} SMs x lanes x {SM_MAX_MHZ:.0f} MHz",
+    digest = sources_sha256()
+    traffic = None
+    if TRAFFIC_CAPTURE["bytes_per_record"] and TRAFFIC_CAPTURE["sources_sha256"] == digest:
+        traffic = TRAFFIC_CAPTURE["bytes_per_record"] * n
+    roof.update(traffic=traffic, traffic_unit="bytes per launch",
+                traffic_source=(TRAFFIC_CAPTURE["summary"] if traffic else
+                                "null: no ncu capture of these kernel sources"),
+                sources_sha256=digest, peak_basis=f"{sm_count} SMs x lanes x {SM_MAX_MHZ:.0f} MHz",
                 pipes=dict(fp32=dict(achieved_tflops=ach_fp32, frac=frac_fp32,
                                      flops_per_record=fl),
                            xu=dict(achieved_tops=ach_xu, frac=frac_xu, ops_per_record=xu)),
@@ -338,7 +366,7 @@ def main():
         # ------------------------------------------ end to end, host buffers --
         hin = api.pinned_records(rec)
         hout = api.pinned_fused_outputs(n)
-        pipe = api.HostPipeline(M, chunk=1 << 21)
+        pipe = api.HostPipeline(M, chunk=1 << 21)   # the C ABI's host-buffer pipeline
         pipe.run(hin, hout)
         torch.cuda.synchronize()
         e2e_steps = max(3, args.steps // 4)

@@ -232,6 +232,29 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
                    void* workspace, size_t workspace_bytes, void* stream,
                    bysdf_launch_config* best);
 
+/* ---- records in host memory ----------------------------------------------
+ * A pipeline streams records held in host memory (pinned, for overlap)
+ * through the fused eval + sample kernel in chunks: the copy of chunk c+1 to
+ * the device, the kernel on chunk c and the copy of chunk c-1's results back
+ * run concurrently on three streams owned by the pipeline.  The pipeline
+ * allocates its device slots (two chunks of records, outputs and workspace)
+ * and streams once, at creation; calls allocate nothing.  Host buffers use
+ * the plane layout of the device calls with plane stride n.  The call is
+ * asynchronous on `stream` (it starts after the work queued there and work
+ * queued there afterwards waits for it); the host buffers must stay valid
+ * until it completes.  One call at a time per pipeline. */
+typedef struct bysdf_host_pipeline bysdf_host_pipeline;
+int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with_ratio,
+                               bysdf_host_pipeline** out);
+int bysdf_host_pipeline_destroy(bysdf_host_pipeline* p);
+/* hits: HOST pointers (seg_offsets must be NULL: chunks of unsorted records,
+ * so the tables must fit in shared memory); outputs: HOST pointers as in
+ * bysdf_eval_sample_pdf. */
+int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, const float* u0,
+                               const float* u1, int64_t n, float* f_rgb, float* pdf,
+                               uint8_t* status, float* wo_s, float* weight_s, float* pdf_s,
+                               uint8_t* lobe_status_s, void* stream);
+
 /* Eval without a caller-provided workspace: the same computation and
  * outputs as bysdf_eval, for callers that are not allowed to allocate device
  * memory (for example a renderer plug-in whose host application owns every

@@ -63,6 +63,10 @@ SYMBOLS = [
                                  C.POINTER(Outputs), P, C.c_size_t, P, C.POINTER(LaunchConfig)]),
     ("bysdf_workspace_error", C.c_int, [P, P, C.POINTER(C.c_uint32)]),
     ("bysdf_eval_noalloc", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, P, P]),
+    ("bysdf_host_pipeline_create", C.c_int, [P, C.c_int64, C.c_int, C.POINTER(P)]),
+    ("bysdf_host_pipeline_destroy", C.c_int, [P]),
+    ("bysdf_eval_sample_pdf_host", C.c_int,
+     [P, C.POINTER(Hits), P, P, C.c_int64, P, P, P, P, P, P, P, P]),
 ]
 
 OP_EVAL, OP_SAMPLE, OP_PDF, OP_FUSED, OP_BACKWARD = range(5)

@@ -291,7 +291,7 @@ def bysdf(params: torch.Tensor, mats: Materials, rec: dict, deterministic: bool 
 
 
 # ------------------------------------------------------------ host buffers --
-_IN_KEYS = ("h", "u", "v", "wi", "wo", "u0", "u1", "mat_id")
+_IN_KEYS = ("h", "u", "v", "wi", "wo", "u0", "u1", "mat_id", "ratio")
 _OUT_KEYS = ("f", "pdf", "status", "wo", "weight", "pdf_s", "lobe_status")
 
 
@@ -306,83 +306,51 @@ def pinned_fused_outputs(n: int) -> dict:
     return {k: v.pin_memory() for k, v in o.items()}
 
 
+def _hptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    return t.data_ptr()
+
+
 class HostPipeline:
-    """Eval + pdf + sample of records held in pinned HOST memory: each chunk
-    is copied to the device, run through the fused kernel and copied back,
-    with the copies of one chunk overlapping the kernel of the next (two
-    device slots; copy-in, compute and copy-out streams).  Slot buffers are
-    flat, so a chunk of m records is viewed as contiguous (3, m) planes."""
+    """Records in (pinned) host memory through the fused eval + sample kernel,
+    chunk by chunk, by the library's host pipeline (bysdf_eval_sample_pdf_host):
+    copy-in, kernel and copy-out of consecutive chunks overlap on the
+    pipeline's own streams."""
 
-    _IN_3 = ("wi", "wo")
-    _OUT_3 = ("f", "wo", "weight")
-
-    def __init__(self, mats: Materials, chunk: int, device="cuda"):
+    def __init__(self, mats: Materials, chunk: int, with_ratio: bool = False):
         self.mats = mats
-        self.chunk = chunk
-        self.dev = torch.device(device)
-        self.s_in = torch.cuda.Stream(self.dev)
-        self.s_run = torch.cuda.Stream(self.dev)
-        self.s_out = torch.cuda.Stream(self.dev)
-        self.slots = []
-        for _ in range(2):
-            din = {k: _empty((3 * chunk if k in self._IN_3 else chunk,),
-                             torch.int32 if k == "mat_id" else torch.float32, self.dev)
-                   for k in _IN_KEYS}
-            dout = {k: _empty((3 * chunk if k in self._OUT_3 else chunk,),
-                              torch.uint8 if k in ("status", "lobe_status") else torch.float32,
-                              self.dev) for k in _OUT_KEYS}
-            self.slots.append((din, dout))
-        self.ws = [torch.empty(mats.lib.bysdf_workspace_size(mats.handle, chunk), dtype=torch.uint8,
-                               device=self.dev) for _ in range(2)]
+        h = C.c_void_p()
+        N.check(mats.lib.bysdf_host_pipeline_create(mats.handle, int(chunk), int(with_ratio),
+                                                    C.byref(h)), "bysdf_host_pipeline_create")
+        self.handle = h
 
-    def run(self, host_in: dict, host_out: dict):
+    def close(self):
+        if getattr(self, "handle", None):
+            self.mats.lib.bysdf_host_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, host_in: dict, host_out: dict, stream=None):
         n = int(host_in["h"].shape[0])
-        ev_free = [None, None]
-        main = torch.cuda.current_stream(self.dev)
-        self.s_in.wait_stream(main)
-        self.s_out.wait_stream(main)
-        for c, a in enumerate(range(0, n, self.chunk)):
-            b = min(n, a + self.chunk)
-            m = b - a
-            k = c & 1
-            din, dout = self.slots[k]
-            view_in = {key: (din[key][:3 * m].view(3, m) if key in self._IN_3 else din[key][:m])
-                       for key in _IN_KEYS if key in host_in}
-            view_out = {key: (dout[key][:3 * m].view(3, m) if key in self._OUT_3 else dout[key][:m])
-                        for key in _OUT_KEYS}
-            with torch.cuda.stream(self.s_in):
-                if ev_free[k] is not None:
-                    self.s_in.wait_event(ev_free[k])
-                for key, dst in view_in.items():
-                    src = host_in[key]
-                    if src.dim() == 2:
-                        for p in range(3):
-                            dst[p].copy_(src[p, a:b], non_blocking=True)
-                    else:
-                        dst.copy_(src[a:b], non_blocking=True)
-            e_in = torch.cuda.Event()
-            e_in.record(self.s_in)
-            self.s_run.wait_event(e_in)
-            ws = self.ws[k]
-            N.check(self.mats.lib.bysdf_eval_sample_pdf(
-                self.mats.handle, C.byref(hits_struct(view_in)), _ptr(view_in["u0"]),
-                _ptr(view_in["u1"]), m, _ptr(view_out["f"]), _ptr(view_out["pdf"]),
-                _ptr(view_out["status"]), _ptr(view_out["wo"]), _ptr(view_out["weight"]),
-                _ptr(view_out["pdf_s"]), _ptr(view_out["lobe_status"]), _ptr(ws), ws.numel(),
-                self.s_run.cuda_stream), "bysdf_eval_sample_pdf")
-            e_run = torch.cuda.Event()
-            e_run.record(self.s_run)
-            self.s_out.wait_event(e_run)
-            with torch.cuda.stream(self.s_out):
-                for key, src in view_out.items():
-                    if src.dim() == 2:
-                        for p in range(3):
-                            host_out[key][p, a:b].copy_(src[p], non_blocking=True)
-                    else:
-                        host_out[key][a:b].copy_(src, non_blocking=True)
-            ev_free[k] = torch.cuda.Event()
-            ev_free[k].record(self.s_out)
-        main.wait_stream(self.s_out)
+        hs = N.Hits()
+        hs.h, hs.u, hs.v = _hptr(host_in["h"]), _hptr(host_in["u"]), _hptr(host_in["v"])
+        hs.wi, hs.wo = _hptr(host_in["wi"]), _hptr(host_in["wo"])
+        hs.ratio = _hptr(host_in.get("ratio"))
+        hs.mat_id = _hptr(host_in.get("mat_id"))
+        o = host_out
+        N.check(self.mats.lib.bysdf_eval_sample_pdf_host(
+            self.handle, C.byref(hs), _hptr(host_in["u0"]), _hptr(host_in["u1"]), n,
+            _hptr(o["f"]), _hptr(o["pdf"]), _hptr(o["status"]), _hptr(o["wo"]),
+            _hptr(o["weight"]), _hptr(o["pdf_s"]), _hptr(o["lobe_status"]), _stream(stream)),
+            "bysdf_eval_sample_pdf_host")
 
     @staticmethod
     def bytes_per_record(host_in: dict, host_out: dict):

@@ -239,9 +239,13 @@ size_t ws_tile_start_off() { return kWsCtl; }
 size_t ws_partials_off(int n_mat) { return align_up(kWsCtl + 4 * (size_t)(n_mat + 1), 256); }
 int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
 
+// Defaults measured on GB300 with the benchmark workloads (eval + sample +
+// pdf over 2^24 records; forward + backward over 2^22): 16 warps per SM in
+// CTAs of 512, two records per lane per warp tile.  bysdf_autotune refines
+// them for a given record set.
 bysdf_launch_config default_cfg() {
   bysdf_launch_config c;
-  c.block = 256;
+  c.block = 512;
   c.items = 2;
   c.ctas_per_sm = 0;  // 0: as many as fit
   c.occupancy = 0;
@@ -601,6 +605,195 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
   o.status = status;
   return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, scratch,
                      BYSDF_NOALLOC_SCRATCH_BYTES, st, m->cfg[BYSDF_OP_EVAL], need);
+}
+
+// ------------------------------------------------------ host pipeline -----
+struct bysdf_host_pipeline {
+  const bysdf_materials* m = nullptr;
+  int64_t chunk = 0;
+  bool with_ratio = false;
+  cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+  cudaEvent_t start = nullptr, in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
+  bool out_pending[2] = {false, false};
+  uint8_t* dev = nullptr;   // both slots
+  size_t slot_bytes = 0, ws_bytes = 0;
+};
+
+namespace {
+// Slot layout (bytes, 256-aligned): inputs h u v wi(3) wo(3) u0 u1 mat_id
+// ratio, outputs f(3) pdf wo_s(3) weight(3) pdf_s status lobe_status, then
+// the workspace.
+struct SlotPtrs {
+  float *h, *u, *v, *wi, *wo, *u0, *u1, *ratio;
+  int32_t* mat;
+  float *f, *pdf, *wo_s, *weight, *pdf_s;
+  uint8_t *status, *lstat;
+  void* ws;
+};
+size_t slot_layout(int64_t c, size_t ws_bytes, uint8_t* base, SlotPtrs* p) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    uint8_t* q = base ? base + off : nullptr;
+    off = align_up(off + bytes, 256);
+    return q;
+  };
+  const size_t f1 = sizeof(float) * (size_t)c, f3 = 3 * f1;
+  SlotPtrs t;
+  t.h = (float*)take(f1); t.u = (float*)take(f1); t.v = (float*)take(f1);
+  t.wi = (float*)take(f3); t.wo = (float*)take(f3); t.u0 = (float*)take(f1);
+  t.u1 = (float*)take(f1); t.ratio = (float*)take(f1); t.mat = (int32_t*)take(f1);
+  t.f = (float*)take(f3); t.pdf = (float*)take(f1); t.wo_s = (float*)take(f3);
+  t.weight = (float*)take(f3); t.pdf_s = (float*)take(f1);
+  t.status = take((size_t)c); t.lstat = take((size_t)c);
+  t.ws = take(ws_bytes);
+  if (p) *p = t;
+  return off;
+}
+}  // namespace
+
+int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with_ratio,
+                               bysdf_host_pipeline** out) {
+  if (!m || !out) return fail(BYSDF_E_ARG, "NULL argument");
+  if (chunk < 1024 || chunk > ((int64_t)1 << 28)) return fail(BYSDF_E_ARG, "chunk outside [1024, 2^28]");
+  if ((size_t)m->n_mat * m->stride > kAllSmemMax)
+    return fail(BYSDF_E_UNSUPPORTED, "host pipeline: tables must fit in shared memory");
+  *out = nullptr;
+  bysdf_host_pipeline* p = new bysdf_host_pipeline();
+  p->m = m;
+  p->chunk = chunk;
+  p->with_ratio = with_ratio != 0;
+  p->ws_bytes = bysdf_workspace_size(m, chunk);
+  p->slot_bytes = slot_layout(chunk, p->ws_bytes, nullptr, nullptr);
+  auto bad = [&](cudaError_t e, const char* what) {
+    bysdf_host_pipeline_destroy(p);
+    return fail(BYSDF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->dev, 2 * p->slot_bytes)) != cudaSuccess) return bad(e, "cudaMalloc");
+  if ((e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking)) != cudaSuccess)
+    return bad(e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming)) != cudaSuccess)
+    return bad(e, "cudaEventCreate");
+  for (int k = 0; k < 2; ++k)
+    if ((e = cudaEventCreateWithFlags(&p->in_done[k], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->run_done[k], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->out_done[k], cudaEventDisableTiming)) != cudaSuccess)
+      return bad(e, "cudaEventCreate");
+  *out = p;
+  return BYSDF_OK;
+}
+
+int bysdf_host_pipeline_destroy(bysdf_host_pipeline* p) {
+  if (!p) return BYSDF_OK;
+  if (p->s_in) cudaStreamSynchronize(p->s_in);
+  if (p->s_run) cudaStreamSynchronize(p->s_run);
+  if (p->s_out) cudaStreamSynchronize(p->s_out);
+  for (int k = 0; k < 2; ++k) {
+    if (p->in_done[k]) cudaEventDestroy(p->in_done[k]);
+    if (p->run_done[k]) cudaEventDestroy(p->run_done[k]);
+    if (p->out_done[k]) cudaEventDestroy(p->out_done[k]);
+  }
+  if (p->start) cudaEventDestroy(p->start);
+  if (p->s_in) cudaStreamDestroy(p->s_in);
+  if (p->s_run) cudaStreamDestroy(p->s_run);
+  if (p->s_out) cudaStreamDestroy(p->s_out);
+  if (p->dev) cudaFree(p->dev);
+  delete p;
+  return BYSDF_OK;
+}
+
+int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, const float* u0,
+                               const float* u1, int64_t n, float* f_rgb, float* pdf,
+                               uint8_t* status, float* wo_s, float* weight_s, float* pdf_s,
+                               uint8_t* lobe_status_s, void* stream) {
+  if (!p || !hits) return fail(BYSDF_E_ARG, "NULL argument");
+  if (n < 0) return fail(BYSDF_E_ARG, "n < 0");
+  if (n == 0) return BYSDF_OK;
+  if (!hits->h || !hits->u || !hits->v || !hits->wi || !hits->wo || !u0 || !u1 || !f_rgb ||
+      !pdf || !status || !wo_s || !weight_s || !pdf_s || !lobe_status_s)
+    return fail(BYSDF_E_ARG, "host pipeline: a required buffer is NULL");
+  if (hits->seg_offsets) return fail(BYSDF_E_UNSUPPORTED, "host pipeline: seg_offsets not supported");
+  if ((hits->ratio != nullptr) != p->with_ratio)
+    return fail(BYSDF_E_ARG, "host pipeline: ratio given / not given unlike at creation");
+  cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+  BY_CU(cudaEventRecord(p->start, caller));
+  BY_CU(cudaStreamWaitEvent(p->s_in, p->start, 0));
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+  for (int64_t a = 0, c = 0; a < n; a += p->chunk, ++c) {
+    const int64_t mcount = std::min(p->chunk, n - a);
+    const int k = (int)(c & 1);
+    SlotPtrs s;
+    slot_layout(p->chunk, p->ws_bytes, p->dev + (size_t)k * p->slot_bytes, &s);
+    // the slot's previous results must be copied out before it is refilled
+    if (p->out_pending[k]) BY_CU(cudaStreamWaitEvent(p->s_in, p->out_done[k], 0));
+    const size_t b1 = sizeof(float) * (size_t)mcount;
+    auto in1 = [&](float* d, const float* h) {
+      return cudaMemcpyAsync(d, h + a, b1, H2D, p->s_in);
+    };
+    auto in3 = [&](float* d, const float* h) {
+      cudaError_t e = cudaSuccess;
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(d + q * mcount, h + (size_t)q * n + a, b1, H2D, p->s_in);
+      return e;
+    };
+    BY_CU(in1(s.h, hits->h));
+    BY_CU(in1(s.u, hits->u));
+    BY_CU(in1(s.v, hits->v));
+    BY_CU(in3(s.wi, hits->wi));
+    BY_CU(in3(s.wo, hits->wo));
+    BY_CU(in1(s.u0, u0));
+    BY_CU(in1(s.u1, u1));
+    if (hits->ratio) BY_CU(in1(s.ratio, hits->ratio));
+    if (hits->mat_id)
+      BY_CU(cudaMemcpyAsync(s.mat, hits->mat_id + a, sizeof(int32_t) * mcount, H2D, p->s_in));
+    BY_CU(cudaEventRecord(p->in_done[k], p->s_in));
+    BY_CU(cudaStreamWaitEvent(p->s_run, p->in_done[k], 0));
+    bysdf_hits dh{};
+    dh.h = s.h;
+    dh.u = s.u;
+    dh.v = s.v;
+    dh.wi = s.wi;
+    dh.wo = s.wo;
+    dh.ratio = hits->ratio ? s.ratio : nullptr;
+    dh.mat_id = hits->mat_id ? s.mat : nullptr;
+    bysdf_outputs o{};
+    o.f_rgb = s.f;
+    o.pdf = s.pdf;
+    o.status = s.status;
+    o.wo = s.wo_s;
+    o.weight = s.weight;
+    o.pdf_s = s.pdf_s;
+    o.lobe_status = s.lstat;
+    int rc = run_forward(p->m, BYSDF_OP_FUSED, &dh, s.u0, s.u1, mcount, o, s.ws, p->ws_bytes,
+                         p->s_run, p->m->cfg[BYSDF_OP_FUSED]);
+    if (rc) return rc;
+    BY_CU(cudaEventRecord(p->run_done[k], p->s_run));
+    BY_CU(cudaStreamWaitEvent(p->s_out, p->run_done[k], 0));
+    auto out1 = [&](float* h, const float* d) {
+      return cudaMemcpyAsync(h + a, d, b1, D2H, p->s_out);
+    };
+    auto out3 = [&](float* h, const float* d) {
+      cudaError_t e = cudaSuccess;
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(h + (size_t)q * n + a, d + q * mcount, b1, D2H, p->s_out);
+      return e;
+    };
+    BY_CU(out3(f_rgb, s.f));
+    BY_CU(out1(pdf, s.pdf));
+    BY_CU(cudaMemcpyAsync(status + a, s.status, (size_t)mcount, D2H, p->s_out));
+    BY_CU(out3(wo_s, s.wo_s));
+    BY_CU(out3(weight_s, s.weight));
+    BY_CU(out1(pdf_s, s.pdf_s));
+    BY_CU(cudaMemcpyAsync(lobe_status_s + a, s.lstat, (size_t)mcount, D2H, p->s_out));
+    BY_CU(cudaEventRecord(p->out_done[k], p->s_out));
+    p->out_pending[k] = true;
+  }
+  // later work on the caller's stream waits for the results
+  for (int k = 0; k < 2; ++k)
+    if (p->out_pending[k]) BY_CU(cudaStreamWaitEvent(caller, p->out_done[k], 0));
+  return BYSDF_OK;
 }
 
 int bysdf_sample(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,

@@ -149,12 +149,14 @@ BY_DF xsqrt(const DualF<N>& a) {
   const float s = sqrtf(a.v);
   return dchain(a, s, s > 0.f ? 0.5f / s : 0.f);
 }
-__device__ __forceinline__ float xexp(float x) { return expf(x); }
+// float path: hardware exp2 / log2 based (relative error ~1e-7 for the
+// arguments here, |x| < ~20); duals keep the library versions
+__device__ __forceinline__ float xexp(float x) { return __expf(x); }
 BY_DF xexp(const DualF<N>& a) {
   const float e = expf(a.v);
   return dchain(a, e, e);
 }
-__device__ __forceinline__ float xlog(float x) { return logf(x); }
+__device__ __forceinline__ float xlog(float x) { return __logf(x); }
 BY_DF xlog(const DualF<N>& a) { return dchain(a, logf(a.v), 1.0f / a.v); }
 __device__ __forceinline__ float xatan2(float y, float x) { return atan2f(y, x); }
 template <int N>
@@ -184,6 +186,17 @@ __device__ __forceinline__ void xsincos_turns(const DualF<N>& t, DualF<N>* s, Du
   sincospif(2.0f * t.v, &sv, &cv);
   *s = dchain(t, sv, 2.0f * kPi * cv);
   *c = dchain(t, cv, -2.0f * kPi * sv);
+}
+// sin and cos of 2 pi t for the small per-step phase advances of the ply
+// trace: the float path reduces t to [-1/2, 1/2] exactly and uses the
+// hardware approximations (absolute error ~5e-7); duals use the exact form.
+__device__ __forceinline__ void xsincos_turns_fast(float t, float* s, float* c) {
+  const float r = t - rintf(t);
+  __sincosf((2.0f * kPi) * r, s, c);
+}
+template <int N>
+__device__ __forceinline__ void xsincos_turns_fast(const DualF<N>& t, DualF<N>* s, DualF<N>* c) {
+  xsincos_turns(t, s, c);
 }
 template <class S> __device__ __forceinline__ S xmax0(const S& a) { return vf(a) < 0.f ? S(0.f) : a; }
 

@@ -5,7 +5,7 @@
 namespace bysdf {
 
 template <int OP>
-__global__ void __launch_bounds__(256) k_plain(const KArgs a, int mat, int64_t begin, int64_t end) {
+__global__ void __launch_bounds__(256, 2) k_plain(const KArgs a, int mat, int64_t begin, int64_t end) {
   const int64_t i = begin + (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (i >= end) return;
   const MatDev* m = reinterpret_cast<const MatDev*>(a.table + (size_t)mat * a.stride);

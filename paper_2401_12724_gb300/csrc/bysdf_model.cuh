@@ -161,60 +161,101 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
                                               float wx, float wy, const S& s0v,
                                               const S& c0v, const S& phase_f_v,
                                               NodeGeo<S>& out, int only_ply = -1,
-                                              int ni_known = 0) {
+                                              int ni_known = 0, bool trace_only = false) {
   const float Rp = m.Rp, Rc = m.Rc;
   out.hit = false;
   out.ni = 0;
-  int best = -1;
-  S best_t = S(0.f), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
-  // only_ply >= 0: the closest ply and N_i are known already (from a float
-  // pass over all plies); trace that ply alone
-  const int k_lo = only_ply >= 0 ? only_ply : 0;
-  const int k_hi = only_ply >= 0 ? only_ply + 1 : m.np;
-  for (int k = k_lo; k < k_hi; ++k) {
-    // phase of ply k in the cross-section at the yarn hit: ply 0's phase
-    // turned by 2 pi k / N_p
-    const float rc = m.rot_c[k], rs = m.rot_s[k];
-    const S ck = c0v * rc - s0v * rs, sk = s0v * rc + c0v * rs;
-    // cross-section update: ply centre at the height of the current
-    // intersection, 2D ray / circle intersection there, repeat
-    S t = S(0.f), cx = S(0.f), cy = S(0.f), sp = sk, cp = ck;
-    bool hit = true;
-    for (int n = 0; n < m.nit; ++n) {
-      if (n > 0) {
-        // the helix phase advances by 2 pi kp dz with dz = kappa t
-        S sd, cd;
-        xsincos_turns(mv.kp * (kappa * t), &sd, &cd);
-        cp = ck * cd - sk * sd;
-        sp = sk * cd + ck * sd;
+  // Per ply: start in the cross-section at the yarn hit (t = 0), intersect
+  // the in-plane ray with the ply circle there, move to the cross-section of
+  // that intersection and repeat, N_it updates; an update whose circle the
+  // ray misses marks the ply "not hit".
+  const int n_re = m.nit < 2 ? m.nit : 2;
+  int best = -1, n_upd = m.nit;
+  float t_start = 0.f;
+  if (only_ply >= 0) {
+    // the closest ply and N_i are known already (from a float pass over all
+    // plies): trace that ply alone, all N_it updates in S
+    best = only_ply;
+    out.ni = ni_known;
+  } else {
+    // Float pass over all plies, to pick the closest ply and count N_i.  The
+    // ply centre c = R_c (cos, sin)(psi_k + 2 pi kp kappa t) enters an update
+    // only through b = (X0 - c).e and perp = (X0 - c) x e, which are linear
+    // in (cos, sin) of the phase advance: with A_k = R_c (cos psi_k, sin
+    // psi_k).e and B_k = R_c (cos psi_k, sin psi_k) x e, an update is 4 FMAs
+    // and one hardware sin/cos.  Every ply runs all N_it updates (a miss is
+    // a flag, not a break), so the lanes of a warp -- one material, hence one
+    // N_p, after the tile sort -- never diverge here.  The closest ply's last
+    // n_re updates are run again below with the correctly rounded sin/cos, so
+    // the hit carries float32 rounding only (the earlier updates reach it
+    // damped by the contraction of the map).
+    const float kk = vf(mv.kp) * kappa;
+    const float bx0 = X0x * ex + X0y * ey, px0 = X0x * ey - X0y * ex;
+    const float c0 = vf(c0v), s0 = vf(s0v);
+    const float A0 = Rc * (c0 * ex + s0 * ey), B0 = Rc * (c0 * ey - s0 * ex);
+    const float Rp2 = Rp * Rp;
+    float best_t = 0.f;
+    for (int k = 0; k < m.np; ++k) {
+      const float rc = m.rot_c[k], rs = m.rot_s[k];
+      const float A = A0 * rc + B0 * rs, Bk = B0 * rc - A0 * rs;
+      float t = 0.f, t_re = 0.f;
+      bool hit = true;
+      auto update = [&]() {
+        float sd, cd;
+        xsincos_turns_fast(kk * t, &sd, &cd);
+        const float bb = bx0 - fmaf(cd, A, sd * Bk);
+        const float perp = px0 - fmaf(cd, Bk, -(sd * A));
+        const float disc = fmaf(-perp, perp, Rp2);
+        hit = hit && disc >= 0.f;
+        t = fmaxf(-bb - sqrtf(fmaxf(disc, 0.f)), 0.f);
+      };
+      for (int n = n_re; n < m.nit; ++n) update();
+      t_re = t;
+      for (int n = 0; n < n_re; ++n) update();
+      if (hit) {
+        out.ni += 1;
+        if (best < 0 || t < best_t) {
+          best = k;
+          best_t = t;
+          t_start = t_re;
+        }
       }
-      cx = Rc * cp;
-      cy = Rc * sp;
-      const S qx = X0x - cx, qy = X0y - cy;
-      const S b = qx * ex + qy * ey;
-      const S perp = qx * ey - qy * ex;
-      const S disc = (Rp - perp) * (Rp + perp);
-      if (vf(disc) < 0.f) {
-        hit = false;
-        break;
-      }
-      t = xmax0(-b - xsqrt(disc));
     }
-    if (!hit) continue;
-    out.ni += 1;
-    if (best < 0 || vf(t) < vf(best_t)) {
-      best = k;
-      best_t = t;
-      best_cx = cx;
-      best_cy = cy;
-      best_s = sp;
-      best_c = cp;
-    }
+    if (best < 0) return;
+    n_upd = n_re;
   }
-  if (best < 0) return;
-  if (only_ply >= 0) out.ni = ni_known;
   out.hit = true;
   out.ply = best;
+  if (trace_only) return;
+  // the closest ply's updates in S with sincospif: ply centre, its phase and
+  // the intersection distance of the last one
+  const S ck = c0v * m.rot_c[best] - s0v * m.rot_s[best];
+  const S sk = s0v * m.rot_c[best] + c0v * m.rot_s[best];
+  S best_t = S(t_start), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
+  bool grazed = false;
+  for (int i = 0; i < n_upd; ++i) {
+    S sd, cd;
+    xsincos_turns(mv.kp * (kappa * best_t), &sd, &cd);
+    best_c = ck * cd - sk * sd;
+    best_s = sk * cd + ck * sd;
+    best_cx = Rc * best_c;
+    best_cy = Rc * best_s;
+    const S qx = X0x - best_cx, qy = X0y - best_cy;
+    const S b = qx * ex + qy * ey;
+    const S perp = qx * ey - qy * ex;
+    const S disc = (Rp - perp) * (Rp + perp);
+    grazed = grazed || !(vf(disc) > 0.f);
+    best_t = xmax0(-b - xsqrt(xmax0(disc)));
+  }
+  if (grazed) {
+    // the ray grazes the ply within rounding: the dual pass has no
+    // derivative there (the node is dropped, as when its trace misses); the
+    // float pass keeps the tangent point
+    if constexpr (is_dual<S>::value) {
+      out.hit = false;
+      return;
+    }
+  }
   // Sec. 3.4: hit point, ply normal (from the ply centre, in the circular
   // cross-section), ply tangent (derivative of the helix through x)
   const S xx = X0x + best_t * ex, xy = X0y + best_t * ey;
@@ -320,7 +361,8 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
     NodeGeo<S> nd;
     if constexpr (is_dual<S>::value) {
       NodeGeo<float> pick;
-      node_geometry(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick);
+      node_geometry(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick,
+                    -1, 0, true);
       if (!pick.hit) continue;
       node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd,
                     pick.ply, pick.ni);

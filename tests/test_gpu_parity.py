@@ -293,3 +293,22 @@ def test_full_size_sampled_records(orc, api):
     assert set(np.unique(st)) <= {0, 1, 2, 3}
     assert np.isfinite(np_(o["f"])).all() and np.isfinite(np_(o["weight"])).all()
     assert (np_(o["f"]) >= 0).all() and (np_(o["pdf_s"]) >= 0).all()
+
+
+def test_host_pipeline_matches_device_call(api):
+    """Records in pinned host memory, streamed in ragged chunks through the
+    library's host pipeline, give the device-resident call's results."""
+    for with_ratio in (False, True):
+        mats = I.materials(3 if with_ratio else 2)
+        rec = I.records(3 if with_ratio else 2, 0, 50_001)
+        M = api.Materials(mats)
+        d = dev(api, rec)
+        o = api.eval_sample_pdf(M, d)
+        hin = api.pinned_records(rec)
+        hout = api.pinned_fused_outputs(len(rec["h"]))
+        pipe = api.HostPipeline(M, chunk=8192, with_ratio=with_ratio)
+        pipe.run(hin, hout)
+        torch.cuda.synchronize()
+        for k in ("f", "pdf", "status", "wo", "weight", "pdf_s", "lobe_status"):
+            assert np.array_equal(hout[k].numpy(), np_(o[k])), k
+        pipe.close()

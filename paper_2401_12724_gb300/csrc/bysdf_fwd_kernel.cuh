@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
         m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
       }
-      forward_record<OP>(a, *m, reinterpret_cast<const float2*>(m + 1), i, q);
+      // two plies side by side in the trace when registers allow (<= 128)
+      forward_record<OP, (BLOCK * MINB <= 512 ? 2 : 1)>(
+          a, *m, reinterpret_cast<const float2*>(m + 1), i, q);
     }
   });
 }

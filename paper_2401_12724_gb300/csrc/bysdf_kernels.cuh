@@ -119,7 +119,7 @@ __device__ __forceinline__ void load_record(const KArgs& a, int64_t i, bool need
 }
 
 // Forward pass of one record: eval/pdf at hits->wo and/or one sample.
-template <int OP>
+template <int OP, int PLIES = 2>
 __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
                                                const float2* map, int64_t i, Record& q) {
   constexpr bool kEval = (OP & (OPF_EVAL | OPF_PDF)) != 0;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
   Shade<float> s;
   if (eval_ok || samp_ok) {
     const MatVars<float> mv = mat_vars<float>(m);
-    geometry(m, map, mv, q, G);
+    geometry<PLIES>(m, map, mv, q, G);
     st = G.status;
     if (st == ST_OK) make_shade(m, mv, G, q, s);
   }

@@ -154,7 +154,7 @@ __device__ __forceinline__ void fiber_lookup(const float2* map, int T, const S& 
 
 // One footprint node: the camera ray enters at in-plane point X0 with
 // in-plane unit direction e and longitudinal slope kappa (Sec. 3.4).
-template <class S>
+template <class S, int PLIES = 2>
 __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
                                               const MatVars<S>& mv, float X0x, float X0y,
                                               float ex, float ey, float v, float kappa,
@@ -195,23 +195,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     const float A0 = Rc * (c0 * ex + s0 * ey), B0 = Rc * (c0 * ey - s0 * ex);
     const float Rp2 = Rp * Rp;
     float best_t = 0.f;
-    for (int k = 0; k < m.np; ++k) {
-      const float rc = m.rot_c[k], rs = m.rot_s[k];
-      const float A = A0 * rc + B0 * rs, Bk = B0 * rc - A0 * rs;
-      float t = 0.f, t_re = 0.f;
-      bool hit = true;
-      auto update = [&]() {
-        float sd, cd;
-        xsincos_turns_fast(kk * t, &sd, &cd);
-        const float bb = bx0 - fmaf(cd, A, sd * Bk);
-        const float perp = px0 - fmaf(cd, Bk, -(sd * A));
-        const float disc = fmaf(-perp, perp, Rp2);
-        hit = hit && disc >= 0.f;
-        t = fmaxf(-bb - sqrtf(fmaxf(disc, 0.f)), 0.f);
-      };
-      for (int n = n_re; n < m.nit; ++n) update();
-      t_re = t;
-      for (int n = 0; n < n_re; ++n) update();
+    auto consider = [&](int k, bool hit, float t, float t_re) {
       if (hit) {
         out.ni += 1;
         if (best < 0 || t < best_t) {
@@ -219,6 +203,60 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           best_t = t;
           t_start = t_re;
         }
+      }
+    };
+    if constexpr (PLIES == 1) {
+      for (int k = 0; k < m.np; ++k) {
+        const float A = A0 * m.rot_c[k] + B0 * m.rot_s[k];
+        const float Bk = B0 * m.rot_c[k] - A0 * m.rot_s[k];
+        float t = 0.f;
+        bool hit = true;
+        auto update = [&]() {
+          float sd, cd;
+          xsincos_turns_fast(kk * t, &sd, &cd);
+          const float bb = bx0 - fmaf(cd, A, sd * Bk);
+          const float perp = px0 - fmaf(cd, Bk, -(sd * A));
+          const float disc = fmaf(-perp, perp, Rp2);
+          hit = hit && disc >= 0.f;
+          t = fmaxf(-bb - sqrtf(fmaxf(disc, 0.f)), 0.f);
+        };
+        for (int n = n_re; n < m.nit; ++n) update();
+        const float t_re = t;
+        for (int n = 0; n < n_re; ++n) update();
+        consider(k, hit, t, t_re);
+      }
+    } else {
+      // two plies per pass: two independent dependency chains per lane (with
+      // an odd N_p the last pass traces its ply twice and counts it once)
+      for (int k0 = 0; k0 < m.np; k0 += 2) {
+        const bool two = k0 + 1 < m.np;
+        const int k1 = two ? k0 + 1 : k0;
+        const float Aa = A0 * m.rot_c[k0] + B0 * m.rot_s[k0];
+        const float Ba = B0 * m.rot_c[k0] - A0 * m.rot_s[k0];
+        const float Ab = A0 * m.rot_c[k1] + B0 * m.rot_s[k1];
+        const float Bb = B0 * m.rot_c[k1] - A0 * m.rot_s[k1];
+        float ta = 0.f, tb = 0.f;
+        bool ha = true, hb = true;
+        auto update = [&]() {
+          float sa, ca, sb, cb;
+          xsincos_turns_fast(kk * ta, &sa, &ca);
+          xsincos_turns_fast(kk * tb, &sb, &cb);
+          const float ba = bx0 - fmaf(ca, Aa, sa * Ba);
+          const float bb = bx0 - fmaf(cb, Ab, sb * Bb);
+          const float pa = px0 - fmaf(ca, Ba, -(sa * Aa));
+          const float pb = px0 - fmaf(cb, Bb, -(sb * Ab));
+          const float da = fmaf(-pa, pa, Rp2);
+          const float db = fmaf(-pb, pb, Rp2);
+          ha = ha && da >= 0.f;
+          hb = hb && db >= 0.f;
+          ta = fmaxf(-ba - sqrtf(fmaxf(da, 0.f)), 0.f);
+          tb = fmaxf(-bb - sqrtf(fmaxf(db, 0.f)), 0.f);
+        };
+        for (int n = n_re; n < m.nit; ++n) update();
+        const float ta_re = ta, tb_re = tb;
+        for (int n = 0; n < n_re; ++n) update();
+        consider(k0, ha, ta, ta_re);
+        if (two) consider(k1, hb, tb, tb_re);
       }
     }
     if (best < 0) return;
@@ -311,7 +349,9 @@ struct Geo {
   float dg_dsig;
 };
 
-template <class S>
+// PLIES: plies traced side by side in the float pass of the ply trace (2
+// gives each lane two independent dependency chains and costs ~5 registers)
+template <int PLIES = 2, class S>
 __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
                                          const MatVars<S>& mv, const Record& q,
                                          Geo<S>& G) {
@@ -361,13 +401,13 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
     NodeGeo<S> nd;
     if constexpr (is_dual<S>::value) {
       NodeGeo<float> pick;
-      node_geometry(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick,
+      node_geometry<float, PLIES>(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick,
                     -1, 0, true);
       if (!pick.hit) continue;
-      node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd,
+      node_geometry<S, PLIES>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd,
                     pick.ply, pick.ni);
     } else {
-      node_geometry(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd);
+      node_geometry<S, PLIES>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd);
     }
     if (!nd.hit) continue;
     nhit += 1;

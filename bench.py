@@ -239,6 +239,9 @@ def workload_device(api, cfg, rank, count=0):
     seed = None if rank == 0 else I.SEED_BASE + cfg + 1000 * rank
     rec = I.records(cfg, 0, count or None, seed=seed)
     seg = I.seg_offsets(cfg, seed=seed)
+    if seg is not None and count:
+        # the first `count` records of a material-sorted workload
+        seg = np.minimum(seg, int(rec["h"].shape[0]))
     d = api.records_to_device(rec, "cuda", seg)
     return rec, d, seg
 
@@ -265,7 +268,10 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="main workload only, no clocks/e2e/CPU baseline (for ncu)")
     ap.add_argument("--records", type=int, default=0,
-                    help="use only the first N records of the main workload (profiling)")
+                    help="use only the first N records of the workload (profiling)")
+    ap.add_argument("--profile-op", default="fused", choices=["fused", "backward"],
+                    help="with --profile: fused = eval + sample + pdf over workload 2; "
+                         "backward = forward eval + backward over workload 5")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -282,6 +288,10 @@ def main():
     torch.cuda.set_device(local)
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
+
+    if args.profile and args.profile_op == "backward":
+        profile_backward(api, torch, args, rank)
+        return
 
     # ---------------------------------------------- main workload (fused) --
     cfg = MAIN_CFG
@@ -409,6 +419,25 @@ def main():
             line["workloads"] = other_workloads(api, N, torch, args, sm_count)
         line["cpu_baseline"] = cpu_oracle_rate(cfg)
     print(json.dumps(line), flush=True)
+
+
+def profile_backward(api, torch, args, rank):
+    """Forward eval + backward steps over workload 5 (or its first --records
+    records), for a profiler; prints the mean step time."""
+    M = api.Materials(I.materials(5))
+    rec, d, _ = workload_device(api, 5, rank, args.records)
+    n = int(d["h"].shape[0])
+    gf = torch.from_numpy(np.ascontiguousarray(rec["g"])).cuda()
+    f = torch.empty(3, n, device="cuda")
+    st = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gp = torch.empty(M.n_mat, 8, device="cuda")
+
+    def step():
+        api.eval(M, d, with_pdf=False, out=dict(f=f, status=st))
+        api.eval_backward(M, d, gf, out=gp)
+    ms, _ = timed(step, args.steps, args.warmup)
+    print(json.dumps(dict(profile="backward", workload=I.WORKLOAD_NAME[5], records=n,
+                          ms_per_step=ms)), flush=True)
 
 
 def other_workloads(api, N, torch, args, sm_count):

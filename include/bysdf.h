@@ -106,7 +106,11 @@ typedef struct bysdf_hits {
   const int64_t* seg_offsets;/* NULL, or n_mat + 1 offsets: records are sorted
                                 by material and material m owns
                                 [seg_offsets[m], seg_offsets[m+1]); required
-                                when the tables do not fit in shared memory  */
+                                when the tables do not fit in shared memory.
+                                Expected: seg_offsets[0] = 0, nondecreasing,
+                                seg_offsets[n_mat] = n; offsets outside
+                                [0, n] are clamped (records outside a
+                                material's clamped range are not written)  */
 } bysdf_hits;
 
 /* Launch shape of the persistent kernels (chosen by bysdf_autotune). */

@@ -291,9 +291,13 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
         if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid;
       }
       mat = lo;
-      const int64_t s1 = __ldg(a.seg + mat + 1);
-      begin = __ldg(a.seg + mat) + (int64_t)(tile - __ldg(a.tile_start + mat)) * a.tile;
+      // offsets outside [0, n] are clamped: no access outside the records
+      int64_t s0 = __ldg(a.seg + mat), s1 = __ldg(a.seg + mat + 1);
+      s0 = s0 < 0 ? 0 : s0;
+      s1 = s1 > a.n ? a.n : s1;
+      begin = s0 + (int64_t)(tile - __ldg(a.tile_start + mat)) * a.tile;
       end = begin + a.tile < s1 ? begin + a.tile : s1;
+      if (end < begin) end = begin;
       if (mat != cur) {
         __syncwarp();
         if (lane == 0) {

@@ -205,11 +205,25 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
         }
       }
     };
+    // Update 0 starts in the hit's cross-section (no phase advance, no
+    // sin/cos): a ply whose circle the ray misses there is not hit whatever
+    // the later updates give, so only the plies that pass it are iterated.
+    uint32_t todo = 0;
+    for (int k = 0; k < m.np; ++k) {
+      const float perp = px0 - (B0 * m.rot_c[k] - A0 * m.rot_s[k]);
+      if (fmaf(-perp, perp, Rp2) >= 0.f) todo |= 1u << k;
+    }
+    // updates 1 .. N_it - 1; t at the entry of update N_it - n_re is where
+    // the exact re-run starts
+    const int n_mid = m.nit - n_re > 1 ? m.nit - n_re : 1;
     if constexpr (PLIES == 1) {
-      for (int k = 0; k < m.np; ++k) {
+      while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
         const float A = A0 * m.rot_c[k] + B0 * m.rot_s[k];
         const float Bk = B0 * m.rot_c[k] - A0 * m.rot_s[k];
-        float t = 0.f;
+        const float p0 = px0 - Bk;
+        float t = fmaxf(-(bx0 - A) - sqrtf(fmaxf(fmaf(-p0, p0, Rp2), 0.f)), 0.f);
         bool hit = true;
         auto update = [&]() {
           float sd, cd;
@@ -220,22 +234,26 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           hit = hit && disc >= 0.f;
           t = fmaxf(-bb - sqrtf(fmaxf(disc, 0.f)), 0.f);
         };
-        for (int n = n_re; n < m.nit; ++n) update();
-        const float t_re = t;
-        for (int n = 0; n < n_re; ++n) update();
+        for (int n = 1; n < n_mid; ++n) update();
+        const float t_re = m.nit > n_re ? t : 0.f;
+        for (int n = n_mid; n < m.nit; ++n) update();
         consider(k, hit, t, t_re);
       }
     } else {
-      // two plies per pass: two independent dependency chains per lane (with
-      // an odd N_p the last pass traces its ply twice and counts it once)
-      for (int k0 = 0; k0 < m.np; k0 += 2) {
-        const bool two = k0 + 1 < m.np;
-        const int k1 = two ? k0 + 1 : k0;
-        const float Aa = A0 * m.rot_c[k0] + B0 * m.rot_s[k0];
-        const float Ba = B0 * m.rot_c[k0] - A0 * m.rot_s[k0];
-        const float Ab = A0 * m.rot_c[k1] + B0 * m.rot_s[k1];
-        const float Bb = B0 * m.rot_c[k1] - A0 * m.rot_s[k1];
-        float ta = 0.f, tb = 0.f;
+      // two plies per pass: two independent dependency chains per lane
+      while (todo) {
+        const int ka = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const bool two = todo != 0;
+        const int kb = two ? __ffs(todo) - 1 : ka;
+        todo &= todo - 1;
+        const float Aa = A0 * m.rot_c[ka] + B0 * m.rot_s[ka];
+        const float Ba = B0 * m.rot_c[ka] - A0 * m.rot_s[ka];
+        const float Ab = A0 * m.rot_c[kb] + B0 * m.rot_s[kb];
+        const float Bb = B0 * m.rot_c[kb] - A0 * m.rot_s[kb];
+        const float pa0 = px0 - Ba, pb0 = px0 - Bb;
+        float ta = fmaxf(-(bx0 - Aa) - sqrtf(fmaxf(fmaf(-pa0, pa0, Rp2), 0.f)), 0.f);
+        float tb = fmaxf(-(bx0 - Ab) - sqrtf(fmaxf(fmaf(-pb0, pb0, Rp2), 0.f)), 0.f);
         bool ha = true, hb = true;
         auto update = [&]() {
           float sa, ca, sb, cb;
@@ -252,11 +270,11 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           ta = fmaxf(-ba - sqrtf(fmaxf(da, 0.f)), 0.f);
           tb = fmaxf(-bb - sqrtf(fmaxf(db, 0.f)), 0.f);
         };
-        for (int n = n_re; n < m.nit; ++n) update();
-        const float ta_re = ta, tb_re = tb;
-        for (int n = 0; n < n_re; ++n) update();
-        consider(k0, ha, ta, ta_re);
-        if (two) consider(k1, hb, tb, tb_re);
+        for (int n = 1; n < n_mid; ++n) update();
+        const float ta_re = m.nit > n_re ? ta : 0.f, tb_re = m.nit > n_re ? tb : 0.f;
+        for (int n = n_mid; n < m.nit; ++n) update();
+        consider(ka, ha, ta, ta_re);
+        if (two) consider(kb, hb, tb, tb_re);
       }
     }
     if (best < 0) return;
@@ -460,10 +478,11 @@ __device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, const S& at, co
   const S ax = at * w.x, ay = ab * w.y;
   return 2.0f * an / (an + xsqrt(an * an + ax * ax + ay * ay));
 }
-// GGX visible-normal sample (Heitz 2018), local frame, w.z > 0.
+// GGX visible-normal sample (Heitz 2018), local frame, w.z > 0; the disk
+// point is (r cos phi, r sin phi) with r = sqrt(u0), phi = 2 pi u1.
 template <class S>
 __device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, const S& at, const S& ab,
-                                             float u0, float u1) {
+                                             float r, float sphi, float cphi) {
   const V3<S> V = normalize(mk3<S>(at * w.x, ab * w.y, w.z));
   const S lensq = V.x * V.x + V.y * V.y;
   V3<S> T1 = lift3<S>(1.f, 0.f, 0.f);
@@ -472,9 +491,6 @@ __device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, const S& at, const 
     T1 = mk3<S>(-(V.y * il), V.x * il, S(0.f));
   }
   const V3<S> T2 = cross(V, T1);
-  float sphi, cphi;
-  sincospif(2.0f * u1, &sphi, &cphi);
-  const float r = sqrtf(u0);
   const float t1 = r * cphi;
   const S s = 0.5f * (1.0f + V.z);
   const S t2 = (1.0f - s) * sqrtf(1.0f - t1 * t1) + s * (r * sphi);
@@ -687,6 +703,10 @@ __device__ __forceinline__ bool sample_dir(const MatDev& m, const Shade<float>& 
   *lobe = k;
   float ur = P[k] > 0.f ? (u0 - lo) / P[k] : 0.f;
   ur = fminf(fmaxf(ur, 0.0f), 0.99999994f);
+  // both samplers map (ur, u1) to the unit disk the same way
+  float sphi, cphi;
+  sincospif(2.0f * u1, &sphi, &cphi);
+  const float r = sqrtf(ur);
   if (k <= 1) {
     // GGX visible normals (Heitz 2018): about n at x for reflection, about
     // the inner normal at y for transmission -- one sampler, frame per lane
@@ -696,7 +716,7 @@ __device__ __forceinline__ bool sample_dir(const MatDev& m, const Shade<float>& 
     const V3<float> T = refl ? s.t : mk3<float>(0.f, 0.f, 1.f);
     const V3<float> B = refl ? s.b : cross(N, T);
     const V3<float> view = refl ? s.wi : s.iy;
-    const V3<float> ml = vndf_sample(to_local(view, T, B, N), s.at, s.ab, ur, u1);
+    const V3<float> ml = vndf_sample(to_local(view, T, B, N), s.at, s.ab, r, sphi, cphi);
     const V3<float> mw = T * ml.x + B * ml.y + N * ml.z;
     const float c = dot(view, mw);
     if (refl) {
@@ -708,9 +728,6 @@ __device__ __forceinline__ bool sample_dir(const MatDev& m, const Shade<float>& 
     *wo = normalize(s.iy * (-m.eta) + mw * (m.eta * c - sqrtf(1.0f - s2t)));
     return dot(*wo, s.ny) > 0.f && dot(*wo, s.n) < 0.f;
   }
-  float sphi, cphi;
-  sincospif(2.0f * u1, &sphi, &cphi);
-  const float r = sqrtf(ur);
   const float zc = sqrtf(fmaxf(0.f, 1.0f - ur)) * (k == 2 ? 1.0f : -1.0f);
   *wo = s.t * (r * cphi) + s.b * (r * sphi) + s.n * zc;
   return true;

@@ -52,23 +52,33 @@ OPS = {
 # dram__bytes_write.sum of one launch on the first 2^22 records of the
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
-# the ones captured (SHA-256 over csrc/ and include/bysdf.h).
-TRAFFIC_CAPTURE = dict(sources_sha256=None, bytes_per_record=None,
+# the ones captured (SHA-256 of FUSED_SOURCES).
+TRAFFIC_CAPTURE = dict(sources_sha256="5a9f42b16d38e92072699d6739475b444b2c37764ef18b47a1bda9db005657ad",
+                       bytes_per_record=85.10,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM
 SM_MAX_MHZ = 2070.0
 
 
+# the files that decide the fused kernel's code and its tables
+FUSED_SOURCES = ("paper_2401_12724_gb300/csrc/bysdf_fwd_fused.cu",
+                 "paper_2401_12724_gb300/csrc/bysdf_fwd_kernel.cuh",
+                 "paper_2401_12724_gb300/csrc/bysdf_kernels.cuh",
+                 "paper_2401_12724_gb300/csrc/bysdf_model.cuh",
+                 "paper_2401_12724_gb300/csrc/bysdf_common.cuh",
+                 "paper_2401_12724_gb300/csrc/bysdf_launch.h",
+                 "paper_2401_12724_gb300/csrc/bysdf_api.cu",
+                 "paper_2401_12724_gb300/build.py",
+                 "include/bysdf.h")
+
+
 def sources_sha256() -> str:
-    """Digest of the CUDA sources and the C header (file names and bytes)."""
+    """Digest of the fused kernel's sources (file names and bytes)."""
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2401_12724_gb300", "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
-                   if f.endswith((".cu", ".cuh", ".h")))
-    for path in files + [os.path.join(ROOT, "include", "bysdf.h")]:
-        h.update(os.path.basename(path).encode())
-        with open(path, "rb") as fh:
+    for rel in FUSED_SOURCES:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
@@ -261,7 +271,7 @@ def sorted_copy(d, n_mat):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--main-only", action="store_true", help="skip the other workloads")

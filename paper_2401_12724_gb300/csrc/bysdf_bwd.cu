@@ -25,23 +25,29 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
     for (int64_t i = begin + lane; i < end; i += 32) {
       Record q;
       load_record(a, i, true, false, q);
-      float g[8];
+      // one call site of the (large, dual-number) record body for both
+      // scheduling modes keeps the kernel's code small
+      int mm;
+      const uint8_t* tb;
       if (mat >= 0) {
         q.mat = mat;
-        const MatDev* m = reinterpret_cast<const MatDev*>(slot);
-        backward_record(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += g[k];
+        mm = mat;
+        tb = slot;
       } else {
         q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
-        const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
-        const MatDev* m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
-        backward_record(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
-        if (q.mat == mm) {
+        mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
+        tb = smem + (size_t)mm * a.stride;
+      }
+      const MatDev* m = reinterpret_cast<const MatDev*>(tb);
+      float g[8];
+      backward_record(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
+      if (mat >= 0) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (g[k] != 0.f) atomicAdd(&sacc[mm * 8 + k], g[k]);
-        }
+        for (int k = 0; k < 8; ++k) acc[k] += g[k];
+      } else if (q.mat == mm) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (g[k] != 0.f) atomicAdd(&sacc[mm * 8 + k], g[k]);
       }
     }
     if (mat >= 0) {

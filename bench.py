@@ -42,11 +42,11 @@ MAIN_CFG = 2
 # scalar on 4096 records of each workload (oracle/count_ops.py): FP32 flops
 # (adds + multiplies) and XU ops (divisions, square roots, transcendentals).
 OPS = {
-    1: dict(eval=(461.2, 63.5)),
-    2: dict(eval=(499.9, 69.1), fused=(673.5, 88.1)),
-    3: dict(eval=(2902.8, 431.6), fused=(3082.3, 451.1)),
-    4: dict(eval=(541.0, 75.0), fused=(720.8, 94.6)),
-    5: dict(eval=(397.7, 54.2)),
+    1: dict(eval=(476.2, 67.9)),
+    2: dict(eval=(515.3, 73.6), fused=(695.9, 92.6)),
+    3: dict(eval=(2941.7, 458.5), fused=(3128.3, 478.0)),
+    4: dict(eval=(557.1, 79.7), fused=(744.2, 99.3)),
+    5: dict(eval=(412.0, 58.6)),
 }
 # DRAM traffic of the fused kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch on the first 2^22 records of the

@@ -11,6 +11,7 @@ tests under ``tests/test_oracle_*.py`` (closed forms, brute force, invariants).
 """
 from .oracle import (  # noqa: F401
     NPARAM,
+    NPARAM_EXT,
     build,
     count_ops,
     eval_records,
@@ -20,6 +21,7 @@ from .oracle import (  # noqa: F401
     geometry,
     ggx_d,
     ggx_g1,
+    grad_ext_records,
     grad_records,
     layout,
     lib,

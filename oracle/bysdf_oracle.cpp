@@ -180,7 +180,8 @@ Layout make_layout(const orc_material& d) {
       !(d.yarn_radius > 0.0) || d.map_texels < 4 || d.map_texels > 4096 ||
       d.trace_iters < 1 || d.trace_iters > 64 || d.k_max < 1 || d.k_max > 64 ||
       !(d.eta > 1.0) || !(d.body_B >= 0.0 && d.body_B <= 1.0) ||
-      !(d.body_r >= 0.0 && d.body_r <= 1.0))
+      !(d.body_r >= 0.0 && d.body_r <= 1.0) || !std::isfinite(d.albedo_y[0]) ||
+      !std::isfinite(d.albedo_y[1]) || !std::isfinite(d.albedo_y[2]))
     return L;
   L.R = d.yarn_radius;
   if (d.n_plies == 1) {
@@ -281,13 +282,20 @@ struct Mat {
   const MatStatic* st;
   S alb[3], beta_t, beta_b, alpha_p, alpha_f, sigma_s;
   S omega_p, omega_f;  // angular rates of the ply and fiber helices (rad / length)
+  // Sec. 4.1.3 / 4.1.5 weights and Eq. 4 attenuation (the paper's fitting set)
+  S body_r, body_B, sigma_t, k_spec;
+  S alb_y[3];  // k^B_y of Eq. 6 (equal to alb unless the material sets it)
 };
 
 template <class S> void seed(S&, int) {}
-template <int N> void seed(Dual<N>& x, int k) { x.d[k] = 1.0; }
+template <int N> void seed(Dual<N>& x, int k) {
+  if (k < N) x.d[k] = 1.0;
+}
 
+// ext: seed the 15 parameters of ORC_NPARAM_EXT; otherwise the 8 of
+// ORC_NPARAM, where the albedo tangent moves k^B_x and k^B_y together
 template <class S>
-Mat<S> make_mat(const MatStatic& st, bool with_tangents) {
+Mat<S> make_mat(const MatStatic& st, bool with_tangents, bool ext = false) {
   using std::tan;
   Mat<S> m;
   m.st = &st;
@@ -298,13 +306,25 @@ Mat<S> make_mat(const MatStatic& st, bool with_tangents) {
   m.alpha_p = S(d.ply_twist_deg * PI / 180.0);
   m.alpha_f = S(d.fiber_twist_deg * PI / 180.0);
   m.sigma_s = S(d.shadow_density);
+  m.body_r = S(d.body_r);
+  m.body_B = S(d.body_B);
+  m.sigma_t = S(d.sigma_t);
+  m.k_spec = S(d.k_spec);
+  for (int c = 0; c < 3; ++c) m.alb_y[c] = S(d.albedo_y[c] < 0.0 ? d.albedo[c] : d.albedo_y[c]);
   if (with_tangents) {
-    for (int c = 0; c < 3; ++c) seed(m.alb[c], ORC_P_ALB_R + c);
+    for (int c = 0; c < 3; ++c) {
+      seed(m.alb[c], ORC_P_ALB_R + c);
+      seed(m.alb_y[c], ext ? ORC_P_ALBY_R + c : ORC_P_ALB_R + c);
+    }
     seed(m.beta_t, ORC_P_BETA_T);
     seed(m.beta_b, ORC_P_BETA_B);
     seed(m.alpha_p, ORC_P_ALPHA_P);
     seed(m.alpha_f, ORC_P_ALPHA_F);
     seed(m.sigma_s, ORC_P_SIGMA_S);
+    seed(m.body_r, ORC_P_BODY_R);
+    seed(m.body_B, ORC_P_BODY_B);
+    seed(m.sigma_t, ORC_P_SIGMA_T);
+    seed(m.k_spec, ORC_P_K_SPEC);
   }
   // Helix about the yarn axis at radius R_c with helix angle alpha_p; a single
   // ply sits on the axis and does not wind (Sec. 3.4).
@@ -396,7 +416,7 @@ void fiber_lookup(const MatStatic& st, const S& theta_f, S* delta, S* of) {
 // diameter.  psi_k is the phase of ply k in that cross-section.
 template <class S>
 S ply_occlusion(const Mat<S>& m, int k, const S& psi_k, const S& xx, const S& xy,
-                double wx, double wy) {
+                const S& wx, const S& wy) {
   using std::cos;
   using std::sin;
   using std::sqrt;
@@ -422,7 +442,7 @@ S ply_occlusion(const Mat<S>& m, int k, const S& psi_k, const S& xx, const S& xy
 
 template <class S>
 Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
-                      double ey, double v, double kappa, const double* wi) {
+                      double ey, double v, const S& kappa, const V3<S>& wi) {
   using std::atan2;
   using std::cos;
   using std::exp;
@@ -496,9 +516,9 @@ Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
   g.tf = g.tp * cos(m.alpha_f) + ep * sin(m.alpha_f);
   g.nf = g.np * cos(g.delta) + cross(g.tf, g.np) * sin(g.delta);
   // Sec. 4.1.4: shadowing terms G = exp(-sigma_s * occlusion).
-  const double wl = std::sqrt(wi[0] * wi[0] + wi[1] * wi[1]);
+  const S wl = sqrt(wi.x * wi.x + wi.y * wi.y);
   S op = S(0.0);
-  if (wl > 1e-7) op = ply_occlusion(m, best, best_psi, xx, xy, wi[0] / wl, wi[1] / wl);
+  if (val(wl) > 1e-7) op = ply_occlusion(m, best, best_psi, xx, xy, wi.x / wl, wi.y / wl);
   g.gp = exp(-m.sigma_s * op);
   g.gf = exp(-m.sigma_s * g.of);
   return g;
@@ -544,7 +564,8 @@ struct Geo {
 // averaged (normal, tangent, shadowing, hit point, N_i), nodes without a ply
 // hit are dropped.  K = 1 at h0 is the near field (Sec. 4.1).
 template <class S>
-Geo<S> geometry(const Mat<S>& m, const Rec& q) {
+Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi) {
+  using std::sqrt;
   const MatStatic& st = *m.st;
   Geo<S> G;
   G.fp = footprint(q.h, q.has_ratio, q.ratio, st.d.k_max);
@@ -552,9 +573,9 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q) {
   // longitudinal slope from omega_i . T.
   const double g0 = std::asin(q.h);
   const double ex = -std::cos(q.u - g0), ey = -std::sin(q.u - g0);
-  const double Lxy = std::sqrt(q.wi[0] * q.wi[0] + q.wi[1] * q.wi[1]);
-  if (Lxy < 1e-7) return G;
-  const double kappa = -q.wi[2] / Lxy;
+  const S Lxy = sqrt(wi.x * wi.x + wi.y * wi.y);
+  if (val(Lxy) < 1e-7) return G;
+  const S kappa = -wi.z / Lxy;
   V3<S> ns = mk<S>(S(0.0), S(0.0), S(0.0)), ts = ns, xs = ns;
   S gs = S(0.0), nis = S(0.0);
   const int K = G.fp.K;
@@ -562,7 +583,7 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q) {
     const double hj = (double)G.fp.h1 + ((j + 0.5) * (double)G.fp.width) / K;
     const double uj = (q.u - g0) + std::asin(hj);
     const double X0x = st.L.R * std::cos(uj), X0y = st.L.R * std::sin(uj);
-    Node<S> nd = node_geometry(m, X0x, X0y, ex, ey, q.v, kappa, q.wi);
+    Node<S> nd = node_geometry(m, X0x, X0y, ex, ey, q.v, kappa, wi);
     if (j == 0) G.node0 = nd;
     if (!nd.hit) continue;
     G.nhit += 1;
@@ -586,6 +607,10 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q) {
   G.ni = nis * inv;
   G.status = ORC_OK;
   return G;
+}
+template <class S>
+Geo<S> geometry(const Mat<S>& m, const Rec& q) {
+  return geometry(m, q, lift<S>(q.wi));
 }
 
 // -------------------------------------------------------------- microfacet --
@@ -650,8 +675,9 @@ V3<S> to_local(const V3<S>& w, const V3<S>& t, const V3<S>& b, const V3<S>& n) {
 template <class S>
 struct Shade {
   V3<S> t, b, n, wi;
-  S mui, at, ab, ks, g, alb[3];
-  double eta, B, r;
+  S mui, at, ab, ks, g, alb[3], alb_y[3];
+  double eta;
+  S B = S(0.0), r = S(0.0);
   // transmission path through the yarn (TT lobe)
   bool tt_ok = false;
   V3<S> iy, ty, by, ny;
@@ -667,12 +693,12 @@ S clamp_alpha(const S& a) {
 }
 
 template <class S>
-Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const double* wi) {
+Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi) {
   using std::exp;
   using std::sqrt;
   const orc_material& d = m.st->d;
   Shade<S> s;
-  s.wi = lift<S>(wi);
+  s.wi = wi;
   s.n = G.n;
   s.t = G.t;
   s.b = cross(s.n, s.t);
@@ -688,11 +714,14 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const double* wi) {
   s.at = clamp_alpha(m.beta_t + half_w);
   s.ab = clamp_alpha(m.beta_b + half_w);
   s.eta = d.eta;
-  s.B = d.body_B;
-  s.r = d.body_r;
-  s.ks = S((1.0 - d.body_B) * d.k_spec);
+  s.B = m.body_B;
+  s.r = m.body_r;
+  s.ks = (1.0 - m.body_B) * m.k_spec;
   s.g = G.g;
-  for (int c = 0; c < 3; ++c) s.alb[c] = m.alb[c];
+  for (int c = 0; c < 3; ++c) {
+    s.alb[c] = m.alb[c];
+    s.alb_y[c] = m.alb_y[c];
+  }
   s.fr = fresnel(s.mui, d.eta);
   // Sec. 4.1.1, reading: the camera ray refracts smoothly into the yarn at x
   // (transmittance 1 - F), travels straight to the yarn surface y, and is
@@ -715,10 +744,14 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const double* wi) {
   s.by = cross(s.ny, s.ty);
   s.iy = -din;
   s.path = sy;
-  s.tau = exp(-d.sigma_t * G.ni * sy);
+  s.tau = exp(-(m.sigma_t * G.ni * sy));
   s.tx = 1.0 - s.fr;
   s.tt_ok = true;
   return s;
+}
+template <class S>
+Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const double* wi) {
+  return make_shade(m, G, lift<S>(wi));
 }
 
 // The four lobes at omega_o, cosine-weighted (f |omega_o . n|), and the
@@ -759,7 +792,7 @@ Lobes<S> eval_lobes(const Shade<S>& s, const V3<S>& wo) {
     L.pxb = muo / PI;
   } else if (muo < 0.0) {
     // Eq. 6: forward body, Lambertian on the far side.
-    for (int c = 0; c < 3; ++c) L.fyb[c] = (1.0 - s.r) * s.B * s.g * s.alb[c] / PI * (-muo);
+    for (int c = 0; c < 3; ++c) L.fyb[c] = (1.0 - s.r) * s.B * s.g * s.alb_y[c] / PI * (-muo);
     L.pyb = -muo / PI;
     // Eq. 3 (third case times the second, Walter's transmission term), at the
     // exit point y from inside (eta) to outside (1), times tau^{N_i}.
@@ -792,11 +825,11 @@ Lobes<S> eval_lobes(const Shade<S>& s, const V3<S>& wo) {
 // into reflection / transmission; body B split by r).
 template <class S>
 void lobe_probs(const Shade<S>& s, double* P) {
-  const double fr = val(s.fr);
-  P[0] = (1.0 - s.B) * fr;
-  P[1] = (1.0 - s.B) * (1.0 - fr);
-  P[2] = s.B * s.r;
-  P[3] = s.B * (1.0 - s.r);
+  const double fr = val(s.fr), B = val(s.B), r = val(s.r);
+  P[0] = (1.0 - B) * fr;
+  P[1] = (1.0 - B) * (1.0 - fr);
+  P[2] = B * r;
+  P[3] = B * (1.0 - r);
 }
 
 template <class S>
@@ -819,19 +852,25 @@ struct Out {
   Out() { for (int c = 0; c < 3; ++c) f[c] = weight[c] = S(0.0); }
 };
 
+// wi, wo: the record's directions as scalars of type S (seeded for
+// derivatives with respect to them)
 template <class S>
-Out<S> eval_one(const Mat<S>& m, const Rec& q) {
+Out<S> eval_one(const Mat<S>& m, const Rec& q, const V3<S>& wi, const V3<S>& wo) {
   Out<S> o;
-  const Geo<S> G = geometry(m, q);
+  const Geo<S> G = geometry(m, q, wi);
   if (G.status != ORC_OK) {
     o.status = ORC_NO_HIT;
     return o;
   }
-  const Shade<S> s = make_shade(m, G, q.wi);
-  const Lobes<S> L = eval_lobes(s, lift<S>(q.wo));
+  const Shade<S> s = make_shade(m, G, wi);
+  const Lobes<S> L = eval_lobes(s, wo);
   total(s, L, o.f, &o.pdf);
   o.status = ORC_OK;
   return o;
+}
+template <class S>
+Out<S> eval_one(const Mat<S>& m, const Rec& q) {
+  return eval_one(m, q, lift<S>(q.wi), lift<S>(q.wo));
 }
 
 template <class S>
@@ -1036,6 +1075,55 @@ int orc_grad(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
   for (int k = 0; k < n_mat * ORC_NPARAM; ++k) {
     double s = 0.0;
     for (int t = 0; t < nt; ++t) s += partial[(size_t)t * n_mat * ORC_NPARAM + k];
+    grad[k] = s;
+  }
+  return 0;
+}
+
+int orc_grad_ext(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                 const double* g_rgb, double* grad, double* g_wi, double* g_wo,
+                 double* jac, double* f_rgb, int n_threads) {
+  constexpr int NP = ORC_NPARAM_EXT, NT = NP + 6;  // 15 parameters, wi, wo
+  typedef Dual<NT> D;
+  Batch B = make_batch(m, n_mat);
+  if (!B.ok) return -1;
+  const int nt = std::max(1, n_threads);
+  std::vector<double> partial((size_t)nt * n_mat * NP, 0.0);
+  parallel_for(n, nt, [&](int64_t b, int64_t e, int tid) {
+    std::vector<Mat<D>> mats;
+    for (auto& st : B.st) mats.push_back(make_mat<D>(st, true, true));
+    double* acc = partial.data() + (size_t)tid * n_mat * NP;
+    for (int64_t i = b; i < e; ++i) {
+      const Rec q = read_rec(r, i, n);
+      V3<D> wi = lift<D>(q.wi), wo = lift<D>(q.wo);
+      seed(wi.x, NP + 0);
+      seed(wi.y, NP + 1);
+      seed(wi.z, NP + 2);
+      seed(wo.x, NP + 3);
+      seed(wo.y, NP + 4);
+      seed(wo.z, NP + 5);
+      Out<D> o;
+      if (valid_rec(q, n_mat, true, false)) o = eval_one(mats[q.mat], q, wi, wo);
+      double vw[6] = {0, 0, 0, 0, 0, 0};
+      for (int c = 0; c < 3; ++c) {
+        const double g = g_rgb[c * n + i];
+        if (f_rgb) f_rgb[c * n + i] = o.f[c].v;
+        for (int k = 0; k < NT; ++k) {
+          if (jac) jac[(i * 3 + c) * NT + k] = o.f[c].d[k];
+          if (o.status != ORC_OK) continue;
+          if (k < NP) acc[q.mat * NP + k] += g * o.f[c].d[k];
+          else vw[k - NP] += g * o.f[c].d[k];
+        }
+      }
+      for (int c = 0; c < 3; ++c) {
+        if (g_wi) g_wi[c * n + i] = vw[c];
+        if (g_wo) g_wo[c * n + i] = vw[3 + c];
+      }
+    }
+  });
+  for (int k = 0; k < n_mat * NP; ++k) {
+    double s = 0.0;
+    for (int t = 0; t < nt; ++t) s += partial[(size_t)t * n_mat * NP + k];
     grad[k] = s;
   }
   return 0;

@@ -41,6 +41,8 @@ typedef struct orc_material {
   double sigma_t;          /* extinction coefficient (per unit length) */
   double shadow_density;   /* sigma_s of the shadowing terms */
   double packing;          /* fiber area fraction of a ply cross-section */
+  double albedo_y[3];      /* k^B_y (RGB) of the transmission body lobe (Eq. 6);
+                              negative: equal to albedo */
 } orc_material;
 
 /* Structure-of-arrays hit records; wi/wo are [3][n] planes (x, y, z). */
@@ -62,7 +64,13 @@ enum { ORC_OK = 0, ORC_NO_HIT = 1, ORC_INVALID = 2, ORC_BAD_SAMPLE = 3 };
 /* Index of the differentiable per-material parameters. */
 enum {
   ORC_P_ALB_R = 0, ORC_P_ALB_G, ORC_P_ALB_B, ORC_P_BETA_T, ORC_P_BETA_B,
-  ORC_P_ALPHA_P, ORC_P_ALPHA_F, ORC_P_SIGMA_S, ORC_NPARAM
+  ORC_P_ALPHA_P, ORC_P_ALPHA_F, ORC_P_SIGMA_S, ORC_NPARAM,
+  /* the paper's fitting set (Sec. 5.2): body reflection share r, the body
+   * colours k^B_x (= ALB above) and k^B_y, attenuation sigma_t (Eq. 4); and
+   * the body fraction B and specular scale k_spec.  In the 8-parameter set
+   * ALB moves k^B_x and k^B_y together. */
+  ORC_P_BODY_R = ORC_NPARAM, ORC_P_ALBY_R, ORC_P_ALBY_G, ORC_P_ALBY_B, ORC_P_SIGMA_T,
+  ORC_P_BODY_B, ORC_P_K_SPEC, ORC_NPARAM_EXT
 };
 
 /* Batched entry points.  Return 0, or -1 on a bad material description. */
@@ -79,6 +87,15 @@ int orc_sample(const orc_material* m, int n_mat, const orc_records* r, int64_t n
 int orc_grad(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
              const double* g_rgb, double* grad, double* jac, double* f_rgb,
              int n_threads);
+/* As orc_grad for the 15 parameters of ORC_NPARAM_EXT (grad: [n_mat][15]),
+ * plus, per record, the vector-Jacobian products with respect to the record's
+ * directions: g_wi[c][i] = sum_k g[k][i] df_k/d wi_c and likewise g_wo
+ * ([3][n] each, optional), the partial derivatives of f as a function of the
+ * three components as given (no renormalisation).  jac (optional):
+ * [n][3][21] = 15 parameters, then wi, then wo. */
+int orc_grad_ext(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                 const double* g_rgb, double* grad, double* g_wi, double* g_wo,
+                 double* jac, double* f_rgb, int n_threads);
 /* Operation counts of one evaluation per record.  op: 0 eval (with pdf),
  * 1 sample, 3 the geometry and shading state that eval and sample share.
  * counts: [n][6] = add/sub, mul, div, sqrt, transcendental, compare. */

@@ -13,6 +13,7 @@ _SRC = os.path.join(_HERE, "bysdf_oracle.cpp")
 _HDR = os.path.join(_HERE, "bysdf_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 NPARAM = 8
+NPARAM_EXT = 15   # NPARAM, then r, k^B_y (RGB), sigma_t, B, k_spec
 _lock = threading.Lock()
 _lib = None
 
@@ -37,6 +38,7 @@ class Material(C.Structure):
         ("sigma_t", C.c_double),
         ("shadow_density", C.c_double),
         ("packing", C.c_double),
+        ("albedo_y", C.c_double * 3),
     ]
 
 
@@ -105,6 +107,7 @@ def lib():
         L.orc_pdf.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, C.c_int]
         L.orc_sample.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, C.c_int]
         L.orc_grad.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, C.c_int]
+        L.orc_grad_ext.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, P, P, C.c_int]
         L.orc_count_ops.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_int, P]
         L.orc_geometry.argtypes = [MP, C.c_float, C.c_float, C.c_float, P, C.c_float,
                                    C.POINTER(Geo)]
@@ -154,6 +157,9 @@ def _material(d: dict) -> Material:
     m.sigma_t = f("sigma_t")
     m.shadow_density = f("shadow_density")
     m.packing = f("packing")
+    ay = d.get("albedo_y")
+    for c in range(3):
+        m.albedo_y[c] = -1.0 if ay is None else float(np.float32(ay[c]))
     return m
 
 
@@ -235,6 +241,23 @@ def grad_records(mats, rec, g_rgb, threads: int = 1, jac: bool = False):
                       None if J is None else J.ctypes.data, f.ctypes.data, threads):
         raise ValueError("oracle: bad material description")
     return (grad, f, J) if jac else (grad, f)
+
+
+def grad_ext_records(mats, rec, g_rgb, threads: int = 1, jac: bool = False):
+    """15 parameter gradients [n_mat, 15], the direction vector-Jacobian
+    products g_wi, g_wo [3, n], f [3, n] (and jac [n, 3, 21])."""
+    keep = []
+    M = _materials(mats)
+    r, n = _records(rec, keep)
+    g = np.ascontiguousarray(g_rgb, dtype=np.float64).reshape(3, n)
+    grad = np.zeros((len(mats), NPARAM_EXT)); f = np.zeros((3, n))
+    gwi = np.zeros((3, n)); gwo = np.zeros((3, n))
+    J = np.zeros((n, 3, NPARAM_EXT + 6)) if jac else None
+    if lib().orc_grad_ext(M, len(mats), C.byref(r), n, g.ctypes.data, grad.ctypes.data,
+                          gwi.ctypes.data, gwo.ctypes.data,
+                          None if J is None else J.ctypes.data, f.ctypes.data, threads):
+        raise ValueError("oracle: bad material description")
+    return (grad, gwi, gwo, f, J) if jac else (grad, gwi, gwo, f)
 
 
 def count_ops(mats, rec, op: int = 0):

@@ -228,11 +228,13 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
         auto update = [&]() {
           float sd, cd;
           xsincos_turns_fast(kk * t, &sd, &cd);
-          const float bb = bx0 - fmaf(cd, A, sd * Bk);
-          const float perp = px0 - fmaf(cd, Bk, -(sd * A));
+          const float bb = fmaf(-sd, Bk, fmaf(-cd, A, bx0));
+          const float perp = fmaf(sd, A, fmaf(-cd, Bk, px0));
           const float disc = fmaf(-perp, perp, Rp2);
           hit = hit && disc >= 0.f;
-          t = fmaxf(-bb - sqrtf(fmaxf(disc, 0.f)), 0.f);
+          // a miss gives sqrt(disc < 0) = NaN and fmaxf(NaN, 0) = 0; the
+          // ply is flagged and its t no longer used
+          t = fmaxf(-bb - sqrtf(disc), 0.f);
         };
         for (int n = 1; n < n_mid; ++n) update();
         const float t_re = m.nit > n_re ? t : 0.f;
@@ -259,16 +261,18 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           float sa, ca, sb, cb;
           xsincos_turns_fast(kk * ta, &sa, &ca);
           xsincos_turns_fast(kk * tb, &sb, &cb);
-          const float ba = bx0 - fmaf(ca, Aa, sa * Ba);
-          const float bb = bx0 - fmaf(cb, Ab, sb * Bb);
-          const float pa = px0 - fmaf(ca, Ba, -(sa * Aa));
-          const float pb = px0 - fmaf(cb, Bb, -(sb * Ab));
+          const float ba = fmaf(-sa, Ba, fmaf(-ca, Aa, bx0));
+          const float bb = fmaf(-sb, Bb, fmaf(-cb, Ab, bx0));
+          const float pa = fmaf(sa, Aa, fmaf(-ca, Ba, px0));
+          const float pb = fmaf(sb, Ab, fmaf(-cb, Bb, px0));
           const float da = fmaf(-pa, pa, Rp2);
           const float db = fmaf(-pb, pb, Rp2);
           ha = ha && da >= 0.f;
           hb = hb && db >= 0.f;
-          ta = fmaxf(-ba - sqrtf(fmaxf(da, 0.f)), 0.f);
-          tb = fmaxf(-bb - sqrtf(fmaxf(db, 0.f)), 0.f);
+          // a miss gives sqrt(d < 0) = NaN and fmaxf(NaN, 0) = 0; the ply
+          // is flagged and its t no longer used
+          ta = fmaxf(-ba - sqrtf(da), 0.f);
+          tb = fmaxf(-bb - sqrtf(db), 0.f);
         };
         for (int n = 1; n < n_mid; ++n) update();
         const float ta_re = m.nit > n_re ? ta : 0.f, tb_re = m.nit > n_re ? tb : 0.f;

@@ -289,6 +289,9 @@ def _material_f64(O):
             if f in ("albedo",):
                 for c in range(3):
                     m.albedo[c] = float(d["albedo"][c])
+            elif f == "albedo_y":
+                for c in range(3):
+                    m.albedo_y[c] = float(d["albedo_y"][c]) if "albedo_y" in d else -1.0
             elif f == "beta_deg":
                 for c in range(2):
                     m.beta_deg[c] = float(d["beta_deg"][c])
@@ -298,3 +301,105 @@ def _material_f64(O):
                 setattr(m, f, d[f] if t.__name__.startswith("c_int") else float(d[f]))
         return m
     return mk
+
+
+# Extended parameter set (the paper's fitting set, Sec. 5.2: r, k^B_x, k^B_y,
+# sigma_t; plus B and k_spec) and the record's directions.
+PARAM_FIELDS_EXT = PARAM_FIELDS + [("body_r", None, 1.0), ("albedo_y", 0, 1.0),
+                                   ("albedo_y", 1, 1.0), ("albedo_y", 2, 1.0),
+                                   ("sigma_t", None, 1.0), ("body_B", None, 1.0),
+                                   ("k_spec", None, 1.0)]
+
+
+def perturbed_ext(m, k, eps):
+    d = {kk: (list(vv) if isinstance(vv, list) else vv) for kk, vv in m.items()}
+    field, idx, scale = PARAM_FIELDS_EXT[k]
+    if idx is None:
+        d[field] = d[field] + eps * scale
+    else:
+        d[field][idx] = d[field][idx] + eps * scale
+    return d
+
+
+def _ext_case():
+    m = mat(n_plies=3, ply_twist_deg=28.0, fiber_twist_deg=20.0, beta_deg=[12.0, 9.0],
+            albedo=[0.3, 0.6, 0.8], albedo_y=[0.45, 0.35, 0.7], shadow_density=0.7,
+            body_r=0.4, body_B=0.6, sigma_t=0.8, k_spec=0.9)
+    rec = I.random_records(240, seed=43, wi_mode="cosine", v_max=3.0)
+    rec["ratio"] = np.where(np.arange(240) % 2 == 0, 0.0, 0.3).astype(np.float32)
+    g = np.random.default_rng(43).uniform(-1, 1, (3, 240))
+    return m, rec, g
+
+
+def test_extended_gradient_matches_finite_differences(orc, monkeypatch):
+    # the 15 material parameters: central differences on the float64
+    # descriptor path, branch straddles skipped by a step-halving check
+    import oracle.oracle as O
+    monkeypatch.setattr(O, "_material", _material_f64(O))
+    m, rec, g = _ext_case()
+    _, _, _, f, J = orc.grad_ext_records([m], rec, g, jac=True)
+    assert J.shape == (240, 3, 21)
+    for k in range(15):
+        eps = 1e-6
+        fd = (orc.eval_records([perturbed_ext(m, k, eps)], rec)[0]
+              - orc.eval_records([perturbed_ext(m, k, -eps)], rec)[0]) / (2 * eps)
+        fd2 = (orc.eval_records([perturbed_ext(m, k, 2 * eps)], rec)[0]
+               - orc.eval_records([perturbed_ext(m, k, -2 * eps)], rec)[0]) / (4 * eps)
+        smooth = np.abs(fd - fd2) <= 1e-6 * (1 + np.abs(fd))
+        assert smooth.mean() > 0.8, k
+        for c in range(3):
+            s = smooth[c]
+            np.testing.assert_allclose(J[s, c, k], fd[c, s], rtol=1e-5, atol=1e-7,
+                                       err_msg=f"parameter {k}")
+    # each new parameter moves f somewhere (a dropped dependence fails here)
+    for k in range(8, 15):
+        assert np.abs(J[:, :, k]).max() > 1e-3, k
+
+
+def test_extended_gradient_direction_partials(orc):
+    # d f / d wi_c and d f / d wo_c against central differences of the
+    # oracle's value: the records are float32, so each step is the exact
+    # float32 difference (the value itself is evaluated in float64)
+    m, rec, g = _ext_case()
+    _, gwi, gwo, f, J = orc.grad_ext_records([m], rec, g, jac=True)
+    # small enough not to cross texels of the piecewise-linear fiber maps
+    # (the fiber phase is steep in wi), large against the float32 spacing
+    step = 2.0 ** -20
+    for key, base in (("wi", 15), ("wo", 18)):
+        for c in range(3):
+            def fdiff(h):
+                rp = {k: np.array(v, copy=True) for k, v in rec.items()}
+                rm = {k: np.array(v, copy=True) for k, v in rec.items()}
+                rp[key][c] = (rec[key][c].astype(np.float64) + h).astype(np.float32)
+                rm[key][c] = (rec[key][c].astype(np.float64) - h).astype(np.float32)
+                den = rp[key][c].astype(np.float64) - rm[key][c].astype(np.float64)
+                fp, _, sp = orc.eval_records([m], rp)
+                fm, _, sm = orc.eval_records([m], rm)
+                return (fp - fm) / den, (sp == 0) & (sm == 0)
+            fd, ok1 = fdiff(step)
+            fd2, ok2 = fdiff(2 * step)
+            smooth = (np.abs(fd - fd2) <= 2e-4 * (1 + np.abs(fd))) & ok1 & ok2
+            assert smooth.mean() > 0.6, (key, c)
+            for cc in range(3):
+                s = smooth[cc]
+                np.testing.assert_allclose(J[s, cc, base + c], fd[cc, s], rtol=1e-3, atol=1e-5,
+                                           err_msg=f"{key}[{c}]")
+    # the vector-Jacobian products are the Jacobian contracted with g
+    np.testing.assert_allclose(gwi, np.einsum("ck,kcd->dk", g, J[:, :, 15:18]), rtol=1e-12,
+                               atol=1e-12)
+    np.testing.assert_allclose(gwo, np.einsum("ck,kcd->dk", g, J[:, :, 18:21]), rtol=1e-12,
+                               atol=1e-12)
+
+
+def test_extended_gradient_agrees_with_eight_parameter_set(orc):
+    # with k^B_y tied to the albedo, the 8-parameter albedo derivative moves
+    # both body colours: it is the sum of the two separate ones
+    m, rec, g = _ext_case()
+    m = {k: v for k, v in m.items() if k != "albedo_y"}
+    grad8, f8 = orc.grad_records([m], rec, g)
+    grad15, _, _, f15 = orc.grad_ext_records([m], rec, g)
+    np.testing.assert_array_equal(f8, f15)
+    np.testing.assert_allclose(grad8[:, 0:3], grad15[:, 0:3] + grad15[:, 9:12], rtol=1e-12,
+                               atol=1e-12)
+    np.testing.assert_allclose(grad8[:, 3:8], grad15[:, 3:8], rtol=1e-12, atol=1e-12)
+

@@ -524,9 +524,15 @@ def other_workloads(api, N, torch, args, sm_count):
         api.eval_backward(M, d, gf, out=gp)
     ms_fb, _ = timed(fwd_bwd, max(3, steps // 2), 1)
     ms_f, _ = timed(lambda: api.eval(M, d, with_pdf=False, out=dict(f=f, status=st)), steps, 2)
+    # the extended parameter set (15 columns), and with the per-record
+    # direction products
+    ms_x, _ = timed(lambda: api.eval_backward_ext(M, d, gf), max(3, steps // 4), 1)
+    ms_xd, _ = timed(lambda: api.eval_backward_ext(M, d, gf, dirs=True), max(3, steps // 8), 1)
     res[I.WORKLOAD_NAME[5]] = dict(records_per_s=n / (ms_fb / 1e3), ms=ms_fb, records=n,
                                    forward_only_records_per_s=n / (ms_f / 1e3),
-                                   roofline_frac_forward=frac(OPS[5]["eval"], n, ms_f, sm_count))
+                                   roofline_frac_forward=frac(OPS[5]["eval"], n, ms_f, sm_count),
+                                   backward_ext15_records_per_s=n / (ms_x / 1e3),
+                                   backward_ext15_dirs_records_per_s=n / (ms_xd / 1e3))
     return res
 
 

@@ -57,7 +57,8 @@ extern "C" {
 #define BYSDF_E_UNSUPPORTED (-3) /* a combination this build does not run */
 #define BYSDF_E_WORKSPACE (-4)   /* workspace missing or too small */
 
-#define BYSDF_NPARAM 8 /* differentiable parameters per material, see below */
+#define BYSDF_NPARAM 8      /* differentiable parameters per material, see below */
+#define BYSDF_NPARAM_EXT 15 /* the extended set of bysdf_set_params_ext          */
 
 /* Material descriptor (host).  Sec. 3.4 / 3.5 geometry, Sec. 4.1 appearance.
  * Readings of quantities the paper leaves open are documented with each
@@ -85,6 +86,9 @@ typedef struct bysdf_material_desc {
   float sigma_t;          /* extinction coefficient of Eq. 4 (per length)     */
   float shadow_density;   /* sigma_s: G = exp(-sigma_s * occlusion) (Sec 4.1.4)*/
   float packing;          /* fiber area fraction of a ply disc (0, 1]         */
+  float albedo_y[3];      /* k^B_y (RGB) of the transmission body lobe, Eq. 6;
+                             negative: equal to albedo (one body colour for
+                             both lobes, the default reading)               */
 } bysdf_material_desc;
 
 /* Opaque material table: per-material constants and the 1D fiber normal and
@@ -161,6 +165,18 @@ int bysdf_set_params(bysdf_materials* m, const float* params, void* stream);
 /* Copy the current parameters to a DEVICE array [n_mat][8] (same layout). */
 int bysdf_get_params(const bysdf_materials* m, float* params, void* stream);
 
+/* The extended parameter set: the 8 above (where [0..2] is now k^B_x, the
+ * reflection body colour of Eq. 5), then the rest of the paper's fitting set
+ * (Sec. 5.2: r, k^B_x, k^B_y, sigma_t) and the two energy weights:
+ *   [8] r (body reflect share), [9..11] k^B_y (RGB, Eq. 6), [12] sigma_t
+ *   (Eq. 4), [13] B (body share), [14] k_spec (k^S = (1 - B) k_spec).
+ * DEVICE array params[n_mat][15], stream-ordered.  bysdf_set_params (8
+ * columns) sets k^B_x and k^B_y to the same albedo and keeps [8], [12..14].
+ * Values are not range-checked on the device: B and r outside [0, 1] or
+ * negative colours give meaningless results. */
+int bysdf_set_params_ext(bysdf_materials* m, const float* params, void* stream);
+int bysdf_get_params_ext(const bysdf_materials* m, float* params, void* stream);
+
 /* Workspace bytes the calls below need for n records. */
 size_t bysdf_workspace_size(const bysdf_materials* m, int64_t n);
 
@@ -200,6 +216,22 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
 int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
                         const float* grad_f, float* grad_params, int deterministic,
                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* As bysdf_eval_backward for the 15 parameters of bysdf_set_params_ext
+ * (grad_params[n_mat][15], DEVICE, zeroed by this call; [0..2] and [9..11]
+ * are the separate derivatives in k^B_x and k^B_y), and optionally, per
+ * record, the vector-Jacobian products with respect to the record's
+ * directions (inverse rendering):
+ *   grad_wi[c][i] = sum_k grad_f[k][i] d f_k / d wi_c, likewise grad_wo,
+ * 3 DEVICE planes each or NULL, written for every record (0 where the
+ * status != 0).  The derivatives are the partials of f as a function of the
+ * three components as given (f does not renormalise them).  The direction
+ * products run as a second kernel (forward-mode, 6 tangents) only when one
+ * of them is requested.  workspace: bysdf_workspace_size(). */
+int bysdf_eval_backward_ext(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                            const float* grad_f, float* grad_params, float* grad_wi,
+                            float* grad_wo, int deterministic, void* workspace,
+                            size_t workspace_bytes, void* stream);
 
 /* The plain form, for comparison: one launch per material over
  * material-sorted records, one thread per record, tables read from global

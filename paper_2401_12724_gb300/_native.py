@@ -19,6 +19,7 @@ class MaterialDesc(C.Structure):
         ("eta", C.c_float), ("albedo", C.c_float * 3), ("k_spec", C.c_float),
         ("beta_deg", C.c_float * 2), ("body_B", C.c_float), ("body_r", C.c_float),
         ("sigma_t", C.c_float), ("shadow_density", C.c_float), ("packing", C.c_float),
+        ("albedo_y", C.c_float * 3),
     ]
 
 
@@ -49,6 +50,8 @@ SYMBOLS = [
     ("bysdf_num_materials", C.c_int32, [P]),
     ("bysdf_set_params", C.c_int, [P, P, P]),
     ("bysdf_get_params", C.c_int, [P, P, P]),
+    ("bysdf_set_params_ext", C.c_int, [P, P, P]),
+    ("bysdf_get_params_ext", C.c_int, [P, P, P]),
     ("bysdf_workspace_size", C.c_size_t, [P, C.c_int64]),
     ("bysdf_eval", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_size_t, P]),
     ("bysdf_sample", C.c_int, [P, C.POINTER(Hits), P, P, C.c_int64, P, P, P, P, P, C.c_size_t, P]),
@@ -56,6 +59,8 @@ SYMBOLS = [
     ("bysdf_eval_sample_pdf", C.c_int,
      [P, C.POINTER(Hits), P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_size_t, P]),
     ("bysdf_eval_backward", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, C.c_int, P, C.c_size_t, P]),
+    ("bysdf_eval_backward_ext", C.c_int,
+     [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_plain", C.c_int, [C.c_int, P, C.POINTER(Hits), P, P, P, C.c_int64, P, P, P, P, P, P]),
     ("bysdf_set_launch_config", C.c_int, [P, C.c_int, C.POINTER(LaunchConfig)]),
     ("bysdf_get_launch_config", C.c_int, [P, C.c_int, C.POINTER(LaunchConfig)]),
@@ -70,6 +75,7 @@ SYMBOLS = [
 ]
 
 OP_EVAL, OP_SAMPLE, OP_PDF, OP_FUSED, OP_BACKWARD = range(5)
+NPARAM, NPARAM_EXT = 8, 15
 
 
 def lib_path() -> str:

@@ -47,6 +47,9 @@ def desc_struct(d: dict) -> N.MaterialDesc:
         s.albedo[c] = float(d["albedo"][c])
     for c in range(2):
         s.beta_deg[c] = float(d["beta_deg"][c])
+    ay = d.get("albedo_y")
+    for c in range(3):
+        s.albedo_y[c] = -1.0 if ay is None else float(ay[c])
     return s
 
 
@@ -92,6 +95,20 @@ class Materials:
     def get_params(self, stream=None) -> torch.Tensor:
         p = torch.empty(self.n_mat, 8, dtype=torch.float32, device=self.device)
         N.check(self.lib.bysdf_get_params(self.handle, _ptr(p), _stream(stream)), "bysdf_get_params")
+        return p
+
+    def set_params_ext(self, params: torch.Tensor, stream=None):
+        """The 15 parameters of the extended set (bysdf_set_params_ext)."""
+        p = params.detach().to(device=self.device, dtype=torch.float32).contiguous()
+        assert p.shape == (self.n_mat, N.NPARAM_EXT)
+        N.check(self.lib.bysdf_set_params_ext(self.handle, _ptr(p), _stream(stream)),
+                "bysdf_set_params_ext")
+        self._params_keepalive = p
+
+    def get_params_ext(self, stream=None) -> torch.Tensor:
+        p = torch.empty(self.n_mat, N.NPARAM_EXT, dtype=torch.float32, device=self.device)
+        N.check(self.lib.bysdf_get_params_ext(self.handle, _ptr(p), _stream(stream)),
+                "bysdf_get_params_ext")
         return p
 
     def set_launch_config(self, op: int, block: int, items: int, ctas_per_sm: int = 0,
@@ -221,6 +238,23 @@ def eval_backward(mats: Materials, rec: dict, grad_f: torch.Tensor, deterministi
     return g
 
 
+def eval_backward_ext(mats: Materials, rec: dict, grad_f: torch.Tensor,
+                      deterministic: bool = False, dirs: bool = False, stream=None):
+    """d(sum grad_f * f) / d params for the 15-column extended set, and with
+    dirs=True the per-record products grad_f . df/dwi and . df/dwo (3, n)."""
+    n = _n(rec)
+    dev = rec["h"].device
+    g = _empty((mats.n_mat, N.NPARAM_EXT), torch.float32, dev)
+    gwi = _empty((3, n), torch.float32, dev) if dirs else None
+    gwo = _empty((3, n), torch.float32, dev) if dirs else None
+    gf = grad_f.contiguous()
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_backward_ext(
+        mats.handle, C.byref(hits_struct(rec)), n, _ptr(gf), _ptr(g), _ptr(gwi), _ptr(gwo),
+        int(deterministic), _ptr(ws), ws.numel(), _stream(stream)), "bysdf_eval_backward_ext")
+    return g, gwi, gwo
+
+
 def plain(op: int, mats: Materials, rec: dict, seg_host, stream=None, out=None) -> dict:
     """The per-material-launch comparison form (records sorted by material)."""
     n = _n(rec)
@@ -267,6 +301,17 @@ def default_params(descs) -> torch.Tensor:
     return torch.tensor(np.asarray(rows, np.float64), dtype=torch.float32)
 
 
+def default_params_ext(descs) -> torch.Tensor:
+    """The 15 parameters of the extended set of each descriptor."""
+    base = default_params(descs).double().numpy()
+    rows = []
+    for d, b in zip(descs, base):
+        ay = d.get("albedo_y")
+        ky = [d["albedo"][c] if (ay is None or ay[c] < 0) else ay[c] for c in range(3)]
+        rows.append(list(b) + [d["body_r"], *ky, d["sigma_t"], d["body_B"], d["k_spec"]])
+    return torch.tensor(np.asarray(rows, np.float64), dtype=torch.float32)
+
+
 class BYSDFEval(torch.autograd.Function):
     """f = BYSDF(params; records), differentiable in the per-material
     parameters; backward runs the library's recompute-and-reduce kernel."""
@@ -288,6 +333,38 @@ class BYSDFEval(torch.autograd.Function):
 def bysdf(params: torch.Tensor, mats: Materials, rec: dict, deterministic: bool = False):
     """Differentiable evaluation: returns f (3, n) and status (n,)."""
     return BYSDFEval.apply(params, mats, rec, deterministic)
+
+
+class BYSDFEvalExt(torch.autograd.Function):
+    """f = BYSDF(params15, wi, wo; records): differentiable in the 15
+    parameters of the extended set and in the record directions wi, wo
+    (3, n) -- the latter for inverse rendering through the hit records."""
+
+    @staticmethod
+    def forward(ctx, params, wi, wo, mats, rec, deterministic=False):
+        mats.set_params_ext(params)
+        r = dict(rec)
+        r["wi"] = wi.detach().float().contiguous()
+        r["wo"] = wo.detach().float().contiguous()
+        f, _, st = eval(mats, r, with_pdf=False)
+        ctx.mats, ctx.rec, ctx.det = mats, r, deterministic
+        ctx.mark_non_differentiable(st)
+        return f, st
+
+    @staticmethod
+    def backward(ctx, grad_f, grad_st):
+        dirs = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        g, gwi, gwo = eval_backward_ext(ctx.mats, ctx.rec, grad_f.float().contiguous(), ctx.det,
+                                        dirs=dirs)
+        return (g, gwi if ctx.needs_input_grad[1] else None,
+                gwo if ctx.needs_input_grad[2] else None, None, None, None)
+
+
+def bysdf_ext(params: torch.Tensor, wi: torch.Tensor, wo: torch.Tensor, mats: Materials,
+              rec: dict, deterministic: bool = False):
+    """Differentiable evaluation in the extended parameters and the record
+    directions: returns f (3, n) and status (n,)."""
+    return BYSDFEvalExt.apply(params, wi, wo, mats, rec, deterministic)
 
 
 # ------------------------------------------------------------ host buffers --

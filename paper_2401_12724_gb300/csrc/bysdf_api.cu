@@ -79,8 +79,10 @@ bool host_layout(const bysdf_material_desc& d, HostLayout* L, std::string* why) 
   if (!(d.k_spec >= 0.f) || !fin(d.k_spec)) return bad("k_spec must be >= 0");
   if (!(d.sigma_t >= 0.f) || !fin(d.sigma_t)) return bad("sigma_t must be >= 0");
   if (!(d.shadow_density >= 0.f) || !fin(d.shadow_density)) return bad("shadow_density must be >= 0");
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < 3; ++c) {
     if (!fin(d.albedo[c])) return bad("albedo must be finite");
+    if (!fin(d.albedo_y[c])) return bad("albedo_y must be finite (negative: equal to albedo)");
+  }
   for (int c = 0; c < 2; ++c)
     if (!fin(d.beta_deg[c])) return bad("beta_deg must be finite");
   if (!fin(d.ply_twist_deg) || std::fabs(d.ply_twist_deg) >= 89.f) return bad("ply_twist_deg outside (-89, 89)");
@@ -147,8 +149,8 @@ double map_occlusion(const HostLayout& L, double D) {
   return covered / kPiD;
 }
 
-// Derived constants from the 8 parameters (radians), shared by table
-// creation on the host and parameter updates on the device.
+// Derived constants from the 15 parameters of the extended set (radians),
+// shared by table creation on the host and parameter updates on the device.
 __host__ __device__ void split_hi_lo(double x, float* hi, float* lo) {
   *hi = (float)x;
   *lo = (float)(x - (double)*hi);
@@ -164,6 +166,14 @@ __host__ __device__ void derive_constants(MatDev& m, const double* p) {
   m.alpha_p = (float)p[5];
   m.alpha_f = (float)p[6];
   m.sigma_s = (float)p[7];
+  m.r = (float)p[8];
+  m.alb_y[0] = (float)p[9];
+  m.alb_y[1] = (float)p[10];
+  m.alb_y[2] = (float)p[11];
+  m.sigma_t = (float)p[12];
+  m.B = (float)p[13];
+  m.k_spec = (float)p[14];
+  m.ks = (float)((1.0 - p[13]) * p[14]);
   if (m.np == 1) {
     m.kp_hi = m.kp_lo = 0.f;
     m.dkp = 0.f;
@@ -179,22 +189,51 @@ __host__ __device__ void derive_constants(MatDev& m, const double* p) {
   m.sin_af = (float)sin(p[6]);
 }
 
-__global__ void k_update_params(uint8_t* table, int n_mat, int stride, const float* params) {
+// The 15 parameters of a table entry (the extended layout of the C ABI).
+__host__ __device__ void read_params(const MatDev& m, double* p) {
+  p[0] = m.alb[0];
+  p[1] = m.alb[1];
+  p[2] = m.alb[2];
+  p[3] = m.beta_t;
+  p[4] = m.beta_b;
+  p[5] = m.alpha_p;
+  p[6] = m.alpha_f;
+  p[7] = m.sigma_s;
+  p[8] = m.r;
+  p[9] = m.alb_y[0];
+  p[10] = m.alb_y[1];
+  p[11] = m.alb_y[2];
+  p[12] = m.sigma_t;
+  p[13] = m.B;
+  p[14] = m.k_spec;
+}
+
+// ncol 8: the first 8 parameters, k^B_y set to the albedo, the rest kept;
+// ncol 15: all.
+__global__ void k_update_params(uint8_t* table, int n_mat, int stride, const float* params,
+                                int ncol) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_mat) return;
   MatDev* m = reinterpret_cast<MatDev*>(table + (size_t)i * stride);
-  double p[8];
-  for (int k = 0; k < 8; ++k) p[k] = (double)params[i * 8 + k];
+  double p[BYSDF_NPARAM_EXT];
+  read_params(*m, p);
+  for (int k = 0; k < ncol; ++k) p[k] = (double)params[(size_t)i * ncol + k];
+  if (ncol == BYSDF_NPARAM) {
+    p[9] = p[0];
+    p[10] = p[1];
+    p[11] = p[2];
+  }
   derive_constants(*m, p);
 }
 
-__global__ void k_read_params(const uint8_t* table, int n_mat, int stride, float* params) {
+__global__ void k_read_params(const uint8_t* table, int n_mat, int stride, float* params,
+                              int ncol) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_mat) return;
   const MatDev* m = reinterpret_cast<const MatDev*>(table + (size_t)i * stride);
-  const float p[8] = {m->alb[0], m->alb[1], m->alb[2], m->beta_t,
-                      m->beta_b, m->alpha_p, m->alpha_f, m->sigma_s};
-  for (int k = 0; k < 8; ++k) params[i * 8 + k] = p[k];
+  double p[BYSDF_NPARAM_EXT];
+  read_params(*m, p);
+  for (int k = 0; k < ncol; ++k) params[(size_t)i * ncol + k] = (float)p[k];
 }
 
 // Tile plan: reset the tile counter and the error word; for material-sorted
@@ -379,17 +418,43 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   return BYSDF_OK;
 }
 
+int set_params(bysdf_materials* m, const float* params, int ncol, void* stream) {
+  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
+  if ((uintptr_t)params & 3u) return fail(BYSDF_E_ARG, "params must be 4-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_update_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride,
+                                                          params, ncol);
+  BY_CU(cudaGetLastError());
+  return BYSDF_OK;
+}
+
+int get_params(const bysdf_materials* m, float* params, int ncol, void* stream) {
+  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
+  if ((uintptr_t)params & 3u) return fail(BYSDF_E_ARG, "params must be 4-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_read_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride,
+                                                        params, ncol);
+  BY_CU(cudaGetLastError());
+  return BYSDF_OK;
+}
+
+// ext: 15 gradient columns (else 8); grad_wi / grad_wo: direction
+// vector-Jacobian products (extended call only), each optional.
 int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const float* grad_f,
                  float* grad_params, int deterministic, void* ws, size_t ws_bytes,
-                 cudaStream_t st, const bysdf_launch_config& c) {
+                 cudaStream_t st, const bysdf_launch_config& c, bool ext = false,
+                 float* grad_wi = nullptr, float* grad_wo = nullptr) {
+  const int np = ext ? BYSDF_NPARAM_EXT : BYSDF_NPARAM;
   int rc = check_hits(m, h, true, n);
   if (rc) return rc;
   if ((rc = check_out(grad_params, "grad_params"))) return rc;
   if (n > 0 && (rc = check_out(grad_f, "grad_f"))) return rc;
+  if (grad_wi && (rc = check_out(grad_wi, "grad_wi"))) return rc;
+  if (grad_wo && (rc = check_out(grad_wo, "grad_wo"))) return rc;
   if (deterministic && !h->seg_offsets)
     return fail(BYSDF_E_UNSUPPORTED, "deterministic backward needs material-sorted records");
   if (n == 0) {
-    BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * 8 * m->n_mat, st));
+    BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * np * m->n_mat, st));
     return BYSDF_OK;
   }
   KArgs a;
@@ -397,19 +462,32 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
     return rc;
   a.grad_f = grad_f;
   a.grad_params = grad_params;
+  a.n_param = np;
   a.partials = deterministic ? reinterpret_cast<float*>((uint8_t*)ws + ws_partials_off(m->n_mat))
                              : nullptr;
   const size_t smem = a.mode == MODE_ALL_SMEM
-                          ? (size_t)m->n_mat * m->stride + sizeof(float) * 8 * m->n_mat
+                          ? (size_t)m->n_mat * m->stride + sizeof(float) * np * m->n_mat
                           : (size_t)(c.block / 32) * m->stride;
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
-  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, c.occupancy, smem));
+  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, c.occupancy, ext, smem));
   int occ = 0;
-  BY_CU(backward_occupancy(c.block, c.occupancy, smem, &occ));
-  if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * 8 * m->n_mat, st));
+  BY_CU(backward_occupancy(c.block, c.occupancy, ext, smem, &occ));
+  if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * np * m->n_mat, st));
   if ((rc = plan(m, a, ws, st))) return rc;
-  BY_CU(launch_backward(a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));
+  BY_CU(launch_backward(a, c.block, c.occupancy, ext, grid_for(m, c, occ), smem, st));
   if (deterministic) BY_CU(launch_reduce_partials(a, st));
+  if (grad_wi || grad_wo) {
+    // second pass: the direction products (its own tile plan)
+    a.grad_wi = grad_wi;
+    a.grad_wo = grad_wo;
+    const size_t smem_d = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
+                                                  : (size_t)(c.block / 32) * m->stride;
+    if (smem_d > 48 * 1024) BY_CU(set_dirgrad_smem_limit(c.block, smem_d));
+    int occ_d = 0;
+    BY_CU(dirgrad_occupancy(c.block, smem_d, &occ_d));
+    if ((rc = plan(m, a, ws, st))) return rc;
+    BY_CU(launch_dirgrad(a, c.block, grid_for(m, c, occ_d), smem_d, st));
+  }
   return BYSDF_OK;
 }
 
@@ -483,10 +561,6 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
     m.Rfc_d = L[i].Rfc;
     m.eta = d.eta;
     m.inv_eta = (float)(1.0 / (double)d.eta);
-    m.B = d.body_B;
-    m.r = d.body_r;
-    m.ks = (float)((1.0 - (double)d.body_B) * (double)d.k_spec);
-    m.sigma_t = d.sigma_t;
     m.inv_2Rp = (float)(0.5 / L[i].Rp);
     m.m_over_2pi = (float)(L[i].M / (2.0 * kPiD));
     m.inv_np = (float)(1.0 / d.n_plies);
@@ -495,9 +569,13 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
       m.rot_s[j] = (float)std::sin(2.0 * kPiD * j / d.n_plies);
     }
     const double deg = kPiD / 180.0;
-    const double p[8] = {d.albedo[0], d.albedo[1], d.albedo[2], d.beta_deg[0] * deg,
-                         d.beta_deg[1] * deg, d.ply_twist_deg * deg, d.fiber_twist_deg * deg,
-                         d.shadow_density};
+    double p[BYSDF_NPARAM_EXT] = {d.albedo[0], d.albedo[1], d.albedo[2], d.beta_deg[0] * deg,
+                                  d.beta_deg[1] * deg, d.ply_twist_deg * deg,
+                                  d.fiber_twist_deg * deg, d.shadow_density, d.body_r,
+                                  d.albedo[0], d.albedo[1], d.albedo[2], d.sigma_t, d.body_B,
+                                  d.k_spec};
+    for (int c = 0; c < 3; ++c)
+      if (d.albedo_y[c] >= 0.f) p[9 + c] = d.albedo_y[c];
     derive_constants(m, p);
     float2* map = reinterpret_cast<float2*>(&m + 1);
     for (int t = 0; t < d.map_texels; ++t) {
@@ -550,24 +628,25 @@ int bysdf_destroy_materials(bysdf_materials* m) {
 int32_t bysdf_num_materials(const bysdf_materials* m) { return m ? m->n_mat : 0; }
 
 int bysdf_set_params(bysdf_materials* m, const float* params, void* stream) {
-  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  k_update_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride, params);
-  BY_CU(cudaGetLastError());
-  return BYSDF_OK;
+  return set_params(m, params, BYSDF_NPARAM, stream);
 }
 
 int bysdf_get_params(const bysdf_materials* m, float* params, void* stream) {
-  if (!m || !params) return fail(BYSDF_E_ARG, "materials and params must not be NULL");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  k_read_params<<<(m->n_mat + 127) / 128, 128, 0, st>>>(m->d_table, m->n_mat, m->stride, params);
-  BY_CU(cudaGetLastError());
-  return BYSDF_OK;
+  return get_params(m, params, BYSDF_NPARAM, stream);
+}
+
+int bysdf_set_params_ext(bysdf_materials* m, const float* params, void* stream) {
+  return set_params(m, params, BYSDF_NPARAM_EXT, stream);
+}
+
+int bysdf_get_params_ext(const bysdf_materials* m, float* params, void* stream) {
+  return get_params(m, params, BYSDF_NPARAM_EXT, stream);
 }
 
 size_t bysdf_workspace_size(const bysdf_materials* m, int64_t n) {
   if (!m) return 0;
-  return ws_partials_off(m->n_mat) + sizeof(float) * 8 * (size_t)max_tiles(n, m->n_mat);
+  // per-tile partials of the deterministic backward, up to 15 columns
+  return ws_partials_off(m->n_mat) + sizeof(float) * 16 * (size_t)max_tiles(n, m->n_mat);
 }
 
 int bysdf_eval(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* f_rgb,
@@ -844,6 +923,16 @@ int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_
   return run_backward(m, hits, n, grad_f, grad_params, deterministic, workspace,
                       workspace_bytes, reinterpret_cast<cudaStream_t>(stream),
                       m->cfg[BYSDF_OP_BACKWARD]);
+}
+
+int bysdf_eval_backward_ext(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                            const float* grad_f, float* grad_params, float* grad_wi,
+                            float* grad_wo, int deterministic, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  return run_backward(m, hits, n, grad_f, grad_params, deterministic, workspace,
+                      workspace_bytes, reinterpret_cast<cudaStream_t>(stream),
+                      m->cfg[BYSDF_OP_BACKWARD], true, grad_wi, grad_wo);
 }
 
 int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,

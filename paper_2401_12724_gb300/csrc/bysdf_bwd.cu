@@ -1,27 +1,34 @@
-// Backward kernel of libbysdf: recomputes the forward pass of each record in
-// forward-mode dual numbers (one tangent per differentiable parameter) and
-// reduces sum_c g_c df_c/dtheta per material -- warp shuffles over a
-// single-material warp tile, then one atomic (or one fixed-order partial) per
-// tile; with unsorted records, shared-memory accumulators per CTA.
+// Backward kernels of libbysdf.
+//
+// k_backward: per-material parameter gradients.  Recomputes the forward pass
+// of each record with the helix angles as dual-number tangents (the other
+// parameters in closed form) and reduces sum_c g_c df_c/dtheta per material --
+// warp shuffles over a single-material warp tile, then one atomic (or one
+// fixed-order partial) per tile; with unsorted records, shared-memory
+// accumulators per CTA.  EXT selects the 15-column extended set.
+//
+// k_dirgrad: per-record vector-Jacobian products with respect to the record's
+// directions, forward mode with 6 tangents (wi, wo); no reduction.
 #include "bysdf_launch.h"
 
 namespace bysdf {
 
-template <int BLOCK, int MINB>
+template <int BLOCK, int MINB, bool EXT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
+  constexpr int NP = EXT ? 15 : 8;
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[BLOCK / 32];
   // MODE_ALL_SMEM: per-CTA accumulators behind the tables
   float* sacc = reinterpret_cast<float*>(smem + (size_t)a.n_mat * a.stride);
   if (a.mode == MODE_ALL_SMEM) {
-    for (int k = threadIdx.x; k < a.n_mat * 8; k += BLOCK) sacc[k] = 0.f;
+    for (int k = threadIdx.x; k < a.n_mat * NP; k += BLOCK) sacc[k] = 0.f;
   }
   persistent_loop<BLOCK>(a, smem, bars,
                              [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane,
                                  int tile) {
-    float acc[8];
+    float acc[NP];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+    for (int k = 0; k < NP; ++k) acc[k] = 0.f;
     for (int64_t i = begin + lane; i < end; i += 32) {
       Record q;
       load_record(a, i, true, false, q);
@@ -39,20 +46,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
         tb = smem + (size_t)mm * a.stride;
       }
       const MatDev* m = reinterpret_cast<const MatDev*>(tb);
-      float g[8];
-      backward_record(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
+      float g[NP];
+      backward_record<EXT>(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
       if (mat >= 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += g[k];
+        for (int k = 0; k < NP; ++k) acc[k] += g[k];
       } else if (q.mat == mm) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (g[k] != 0.f) atomicAdd(&sacc[mm * 8 + k], g[k]);
+        for (int k = 0; k < NP; ++k)
+          if (g[k] != 0.f) atomicAdd(&sacc[mm * NP + k], g[k]);
       }
     }
     if (mat >= 0) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < NP; ++k) {
         float v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -61,17 +68,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
       if (lane == 0) {
         if (a.partials) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) a.partials[(size_t)tile * 8 + k] = acc[k];
+          for (int k = 0; k < NP; ++k) a.partials[(size_t)tile * NP + k] = acc[k];
         } else {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) atomicAdd(a.grad_params + (size_t)mat * 8 + k, acc[k]);
+          for (int k = 0; k < NP; ++k) atomicAdd(a.grad_params + (size_t)mat * NP + k, acc[k]);
         }
       }
     }
   });
   if (a.mode == MODE_ALL_SMEM) {
     __syncthreads();
-    for (int k = threadIdx.x; k < a.n_mat * 8; k += BLOCK)
+    for (int k = threadIdx.x; k < a.n_mat * NP; k += BLOCK)
       if (sacc[k] != 0.f) atomicAdd(a.grad_params + k, sacc[k]);
   }
 }
@@ -81,49 +88,135 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
 // shape).
 __global__ void k_reduce_partials(const KArgs a) {
   const int m = blockIdx.x, lane = threadIdx.x;
+  const int np = a.n_param;
   const int t0 = a.tile_start[m], t1 = a.tile_start[m + 1];
-  float acc[8];
+  float acc[16];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] = 0.f;
+  for (int k = 0; k < 16; ++k) acc[k] = 0.f;
   for (int t = t0 + lane; t < t1; t += 32) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] += a.partials[(size_t)t * 8 + k];
+    for (int k = 0; k < 16; ++k)
+      if (k < np) acc[k] += a.partials[(size_t)t * np + k];
   }
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < 16; ++k) {
     float v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) a.grad_params[(size_t)m * 8 + k] = v;
+    if (lane == 0 && k < np) a.grad_params[(size_t)m * np + k] = v;
   }
+}
+
+// Direction vector-Jacobian products of one record: sum_c g_c df_c/dwi and
+// df_c/dwo.  Tangents 0..2: wi, 3..5: wo.  The material's helix angles carry
+// no tangent here; the float pre-pass of the geometry picks each node's ply.
+enum { DD_WI = 0, DD_WO = 3, NDD = 6 };
+__device__ __forceinline__ void dirgrad_record(const KArgs& a, const MatDev& m,
+                                               const float2* map, int64_t i, Record& q,
+                                               float gwi[3], float gwo[3]) {
+  typedef DualF<NDD> D;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gwi[c] = gwo[c] = 0.f;
+  if (!record_valid(q, a.n_mat, true, a.ratio != nullptr, false)) return;
+  const MatVars<D> mv = mat_vars<D>(m, false);
+  V3<D> wi = lift3<D>(q.wi[0], q.wi[1], q.wi[2]);
+  V3<D> wo = lift3<D>(q.wo[0], q.wo[1], q.wo[2]);
+  wi.x.d[DD_WI + 0] = 1.f;
+  wi.y.d[DD_WI + 1] = 1.f;
+  wi.z.d[DD_WI + 2] = 1.f;
+  wo.x.d[DD_WO + 0] = 1.f;
+  wo.y.d[DD_WO + 1] = 1.f;
+  wo.z.d[DD_WO + 2] = 1.f;
+  Geo<D> G;
+  geometry_k<1, D, D>(m, map, mv, q, wi, G);
+  if (G.status != ST_OK) return;
+  Shade<D> s;
+  make_shade(m, mv, G, wi, s);
+  LobeVals<D> L;
+  eval_lobes(m, s, wo, L);
+  const int64_t n = a.n;
+  const float g0 = __ldg(a.grad_f + i), g1 = __ldg(a.grad_f + n + i),
+              g2 = __ldg(a.grad_f + 2 * n + i);
+  const float* kb = L.refl ? m.alb : m.alb_y;
+  const float gs = g0 + g1 + g2;
+  const float gb = g0 * kb[0] + g1 * kb[1] + g2 * kb[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gwi[c] = gs * L.spec.d[DD_WI + c] + gb * L.body.d[DD_WI + c];
+    gwo[c] = gs * L.spec.d[DD_WO + c] + gb * L.body.d[DD_WO + c];
+  }
+}
+
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bars[BLOCK / 32];
+  persistent_loop<BLOCK>(a, smem, bars,
+                             [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane,
+                                 int) {
+    for (int64_t i = begin + lane; i < end; i += 32) {
+      Record q;
+      load_record(a, i, true, false, q);
+      const uint8_t* tb;
+      if (mat >= 0) {
+        q.mat = mat;
+        tb = slot;
+      } else {
+        q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
+        tb = smem + (size_t)mm * a.stride;
+      }
+      const MatDev* m = reinterpret_cast<const MatDev*>(tb);
+      float gwi[3], gwo[3];
+      dirgrad_record(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, gwi, gwo);
+      const int64_t n = a.n;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (a.grad_wi) __stcs(a.grad_wi + c * n + i, gwi[c]);
+        if (a.grad_wo) __stcs(a.grad_wo + c * n + i, gwo[c]);
+      }
+    }
+  });
 }
 
 // occupancy 0: registers as needed (8 warps per SM at 256 threads);
 // occupancy 1: at most 128 registers (16 warps per SM; the rest spills).
-static const void* bwd_fn(int block, int occ) {
+template <bool EXT>
+static const void* bwd_fn_t(int block, int occ) {
   switch (block) {
-    case 128: return occ ? (const void*)k_backward<128, 4> : (const void*)k_backward<128, 1>;
-    case 256: return occ ? (const void*)k_backward<256, 2> : (const void*)k_backward<256, 1>;
-    case 512: return (const void*)k_backward<512, 1>;
+    case 128: return occ ? (const void*)k_backward<128, 4, EXT> : (const void*)k_backward<128, 1, EXT>;
+    case 256: return occ ? (const void*)k_backward<256, 2, EXT> : (const void*)k_backward<256, 1, EXT>;
+    case 512: return (const void*)k_backward<512, 1, EXT>;
+  }
+  return nullptr;
+}
+static const void* bwd_fn(int block, int occ, bool ext) {
+  return ext ? bwd_fn_t<true>(block, occ) : bwd_fn_t<false>(block, occ);
+}
+static const void* dir_fn(int block) {
+  switch (block) {
+    case 128: return (const void*)k_dirgrad<128, 1>;
+    case 256: return (const void*)k_dirgrad<256, 1>;
+    case 512: return (const void*)k_dirgrad<512, 1>;
   }
   return nullptr;
 }
 
-cudaError_t set_backward_smem_limit(int block, int occ, size_t smem) {
-  const void* f = bwd_fn(block, occ);
+cudaError_t set_backward_smem_limit(int block, int occ, bool ext, size_t smem) {
+  const void* f = bwd_fn(block, occ, ext);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t backward_occupancy(int block, int occ, size_t smem, int* ctas) {
-  const void* f = bwd_fn(block, occ);
+cudaError_t backward_occupancy(int block, int occ, bool ext, size_t smem, int* ctas) {
+  const void* f = bwd_fn(block, occ, ext);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block, smem);
 }
 
-cudaError_t launch_backward(const KArgs& a, int block, int occ, int grid, size_t smem,
+cudaError_t launch_backward(const KArgs& a, int block, int occ, bool ext, int grid, size_t smem,
                             cudaStream_t st) {
-  const void* f = bwd_fn(block, occ);
+  const void* f = bwd_fn(block, occ, ext);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<KArgs*>(&a)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, st);
@@ -132,6 +225,25 @@ cudaError_t launch_backward(const KArgs& a, int block, int occ, int grid, size_t
 cudaError_t launch_reduce_partials(const KArgs& a, cudaStream_t st) {
   k_reduce_partials<<<a.n_mat, 32, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t set_dirgrad_smem_limit(int block, size_t smem) {
+  const void* f = dir_fn(block);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t dirgrad_occupancy(int block, size_t smem, int* ctas) {
+  const void* f = dir_fn(block);
+  if (!f) return cudaErrorInvalidValue;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block, smem);
+}
+
+cudaError_t launch_dirgrad(const KArgs& a, int block, int grid, size_t smem, cudaStream_t st) {
+  const void* f = dir_fn(block);
+  if (!f) return cudaErrorInvalidValue;
+  void* args[] = {const_cast<KArgs*>(&a)};
+  return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, st);
 }
 
 }  // namespace bysdf

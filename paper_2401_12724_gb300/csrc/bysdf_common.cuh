@@ -20,7 +20,7 @@ struct alignas(16) MatDev {
   float R, Rp, Rc, Rfc;       // yarn / ply radius, ply-centre radius, fiber ring radius
   float eta, inv_eta, B, r;   // refractive index, body share, body reflect share
   float ks, sigma_t, sigma_s, inv_2Rp;  // (1 - B) k_spec, extinction, shadow density
-  float alb[3], m_over_2pi;   // body albedo, M / (2 pi)
+  float alb[3], m_over_2pi;   // k^B_x, reflection body colour (Eq. 5); M / (2 pi)
   float beta_t, beta_b, alpha_p, alpha_f;  // differentiable angles (radians)
   float kp_hi, kp_lo;         // ply helix rate in turns per length, split hi + lo
   float kf_hi, kf_lo;         // fiber phase rate in map periods per length, split
@@ -29,7 +29,8 @@ struct alignas(16) MatDev {
   float inv_np, pad2, pad3, pad4;
   float rot_c[kMaxPlies], rot_s[kMaxPlies];  // cos, sin of 2 pi j / N_p
   double Rc_d, Rfc_d;         // layout radii in double (derived-constant updates)
-  float pad5[4];
+  float alb_y[3];             // k^B_y, transmission body colour (Eq. 6)
+  float k_spec;               // specular scale (ks = (1 - B) k_spec)
 };
 static_assert(sizeof(MatDev) == 256, "MatDev must be 256 bytes");
 

@@ -37,7 +37,10 @@ struct KArgs {
   uint8_t* lstat_s;
   const float* grad_f;
   float* grad_params;
-  float* partials;       // deterministic backward: [n_tiles][8]
+  float* partials;       // deterministic backward: [n_tiles][n_param]
+  int32_t n_param;       // gradient columns: 8, or 15 (extended set)
+  int32_t pad_np;
+  float *grad_wi, *grad_wo;  // direction backward: 3 planes each, or NULL
   WsCtl* ctl;
   const int32_t* tile_start;
 };
@@ -145,9 +148,10 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
     if (est == ST_OK) {
       LobeVals<float> L;
       eval_lobes(m, s, mk3<float>(q.wo[0], q.wo[1], q.wo[2]), L);
-      f0 = L.spec + m.alb[0] * L.body;
-      f1 = L.spec + m.alb[1] * L.body;
-      f2 = L.spec + m.alb[2] * L.body;
+      const float* kb = L.refl ? m.alb : m.alb_y;  // k^B_x (Eq. 5) or k^B_y (Eq. 6)
+      f0 = L.spec + kb[0] * L.body;
+      f1 = L.spec + kb[1] * L.body;
+      f2 = L.spec + kb[2] * L.body;
       p = total_pdf(m, s, L);
     }
     if (OP & OPF_EVAL) {
@@ -178,9 +182,10 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
         const float pt = total_pdf(m, s, L);
         if (pt > 0.f) {
           const float ip = 1.0f / pt;
-          ww0 = (L.spec + m.alb[0] * L.body) * ip;
-          ww1 = (L.spec + m.alb[1] * L.body) * ip;
-          ww2 = (L.spec + m.alb[2] * L.body) * ip;
+          const float* kb = L.refl ? m.alb : m.alb_y;
+          ww0 = (L.spec + kb[0] * L.body) * ip;
+          ww1 = (L.spec + kb[1] * L.body) * ip;
+          ww2 = (L.spec + kb[2] * L.body) * ip;
           p = pt;
           sst = ST_OK;
         }
@@ -197,13 +202,17 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
   }
 }
 
-// Gradient of sum_c g_c f_c of one record w.r.t. the 8 material parameters.
+// Gradient of sum_c g_c f_c of one record w.r.t. the material parameters:
+// the 8 of the basic set (EXT false; [0..2] moves both body colours) or the
+// 15 of the extended set (EXT true; layout of bysdf_set_params_ext).
+template <bool EXT>
 __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
                                                 const float2* map, int64_t i, Record& q,
-                                                float gout[8]) {
+                                                float* gout) {
   typedef DualF<ND> D;
+  constexpr int NP = EXT ? 15 : 8;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) gout[k] = 0.f;
+  for (int k = 0; k < NP; ++k) gout[k] = 0.f;
   if (!record_valid(q, a.n_mat, true, a.ratio != nullptr, false)) return;
   const MatVars<D> mv = mat_vars<D>(m);
   Geo<D> G;
@@ -217,12 +226,15 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   const int64_t n = a.n;
   const float g0 = __ldg(a.grad_f + i), g1 = __ldg(a.grad_f + n + i),
               g2 = __ldg(a.grad_f + 2 * n + i);
-  // f_c = spec + albedo_c body
+  // f_c = spec + k^B_c body, with k^B = k^B_x (reflection side) or k^B_y
+  const float* kb = L.refl ? m.alb : m.alb_y;
   const float gs = g0 + g1 + g2;
-  const float gb = g0 * m.alb[0] + g1 * m.alb[1] + g2 * m.alb[2];
-  gout[0] = g0 * L.body.v;
-  gout[1] = g1 * L.body.v;
-  gout[2] = g2 * L.body.v;
+  const float gb = g0 * kb[0] + g1 * kb[1] + g2 * kb[2];
+  const float body = L.body.v;
+  const int c0 = (EXT && !L.refl) ? 9 : 0;
+  gout[c0 + 0] = g0 * body;
+  gout[c0 + 1] = g1 * body;
+  gout[c0 + 2] = g2 * body;
   // roughness: d spec / d beta = spec * d ln spec / d alpha (alpha = beta +
   // footprint term, unless clamped)
   gout[3] = s.at_free ? gs * L.spec.v * dln_a[0] : 0.f;
@@ -232,7 +244,17 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   gout[6] = gs * L.spec.d[D_ALPHA_F] + gb * L.body.d[D_ALPHA_F];
   // shadow density: the body lobes are proportional to G
   const float Gv = G.g.v;
-  gout[7] = Gv > 0.f ? gb * L.body.v * (G.dg_dsig / Gv) : 0.f;
+  gout[7] = Gv > 0.f ? gb * body * (G.dg_dsig / Gv) : 0.f;
+  if constexpr (EXT) {
+    // body = r B body_w (reflection side) or (1 - r) B body_w; spec = (1 - B)
+    // k_spec spec_u; the transmission lobe carries tau = exp(-sigma_t N_i
+    // |x - y|) (Eq. 4)
+    const float bw = L.body_w.v, su = L.spec_u.v;
+    gout[8] = gb * (L.refl ? m.B : -m.B) * bw;
+    gout[12] = L.refl ? 0.f : gs * L.spec.v * (-s.ni_sy);
+    gout[13] = gb * (L.refl ? m.r : 1.0f - m.r) * bw - gs * m.k_spec * su;
+    gout[14] = gs * (1.0f - m.B) * su;
+  }
 }
 
 // Shared-memory staging of the material tables and the warp tile loop, common

@@ -46,7 +46,9 @@ struct MatVars {
 };
 
 template <class S>
-__device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m) {
+// seed_params: carry the helix-angle tangents (the parameter backward);
+// false for dual numbers that carry other tangents (the direction backward)
+__device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m, bool seed_params = true) {
   MatVars<S> q;
   q.kp = S(m.kp_hi + m.kp_lo);
   q.kf = S(m.kf_hi + m.kf_lo);
@@ -56,6 +58,7 @@ __device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m) {
   q.beta_t = S(m.beta_t);
   q.beta_b = S(m.beta_b);
   if constexpr (is_dual<S>::value) {
+    if (!seed_params) return q;
     q.kp.d[D_ALPHA_P] = m.dkp;
     q.kf.d[D_ALPHA_F] = m.dkf;
     q.cos_af.d[D_ALPHA_F] = -m.sin_af;
@@ -154,11 +157,13 @@ __device__ __forceinline__ void fiber_lookup(const float2* map, int T, const S& 
 
 // One footprint node: the camera ray enters at in-plane point X0 with
 // in-plane unit direction e and longitudinal slope kappa (Sec. 3.4).
-template <class S, int PLIES = 2>
+// K: the type of the slope kappa and the shadow direction (wx, wy) -- float,
+// or S when the record's direction carries tangents
+template <class S, int PLIES = 2, class K = float>
 __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
                                               const MatVars<S>& mv, float X0x, float X0y,
-                                              float ex, float ey, float v, float kappa,
-                                              float wx, float wy, const S& s0v,
+                                              float ex, float ey, float v, const K& kappa,
+                                              const K& wx, const K& wy, const S& s0v,
                                               const S& c0v, const S& phase_f_v,
                                               NodeGeo<S>& out, int only_ply = -1,
                                               int ni_known = 0, bool trace_only = false) {
@@ -189,7 +194,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     // n_re updates are run again below with the correctly rounded sin/cos, so
     // the hit carries float32 rounding only (the earlier updates reach it
     // damped by the contraction of the map).
-    const float kk = vf(mv.kp) * kappa;
+    const float kk = vf(mv.kp) * vf(kappa);
     const float bx0 = X0x * ex + X0y * ey, px0 = X0x * ey - X0y * ex;
     const float c0 = vf(c0v), s0 = vf(s0v);
     const float A0 = Rc * (c0 * ex + s0 * ey), B0 = Rc * (c0 * ey - s0 * ex);
@@ -373,10 +378,10 @@ struct Geo {
 
 // PLIES: plies traced side by side in the float pass of the ply trace (2
 // gives each lane two independent dependency chains and costs ~5 registers)
-template <int PLIES = 2, class S>
-__device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
-                                         const MatVars<S>& mv, const Record& q,
-                                         Geo<S>& G) {
+template <int PLIES = 2, class S, class K>
+__device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
+                                           const MatVars<S>& mv, const Record& q,
+                                           const V3<K>& wi, Geo<S>& G) {
   G.status = ST_NO_HIT;
   const Footprint fp = footprint(q.h, q.ratio, m.kmax);
   G.width = fp.width;
@@ -385,11 +390,11 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
   float su, cu;
   sincosf(u_rel, &su, &cu);
   const float ex = -cu, ey = -su;
-  const float lxy = sqrtf(q.wi[0] * q.wi[0] + q.wi[1] * q.wi[1]);
-  if (!(lxy >= 1e-7f)) return;
-  const float inv_l = 1.0f / lxy;
-  const float kappa = -q.wi[2] * inv_l;
-  const float wx = q.wi[0] * inv_l, wy = q.wi[1] * inv_l;
+  const K lxy = xsqrt(wi.x * wi.x + wi.y * wi.y);
+  if (!(vf(lxy) >= 1e-7f)) return;
+  const K inv_l = K(1.0f) / lxy;
+  const K kappa = -wi.z * inv_l;
+  const K wx = wi.x * inv_l, wy = wi.y * inv_l;
   // ply 0's phase at the hit's cross-section, and the fiber phase there
   const S turns_v = frac_prod_s(mv.kp, m.kp_hi, m.kp_lo, q.v);
   S s0v, c0v;
@@ -423,13 +428,14 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
     NodeGeo<S> nd;
     if constexpr (is_dual<S>::value) {
       NodeGeo<float> pick;
-      node_geometry<float, PLIES>(m, map, mvf, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0f, c0f, pff, pick,
-                    -1, 0, true);
+      node_geometry<float, PLIES, float>(m, map, mvf, X0x, X0y, ex, ey, q.v, vf(kappa), vf(wx),
+                                         vf(wy), s0f, c0f, pff, pick, -1, 0, true);
       if (!pick.hit) continue;
-      node_geometry<S, PLIES>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd,
-                    pick.ply, pick.ni);
+      node_geometry<S, PLIES, K>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v,
+                                 phase_f_v, nd, pick.ply, pick.ni);
     } else {
-      node_geometry<S, PLIES>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v, phase_f_v, nd);
+      node_geometry<S, PLIES, K>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v,
+                                 phase_f_v, nd);
     }
     if (!nd.hit) continue;
     nhit += 1;
@@ -454,6 +460,12 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
   G.dg_dsig = dgs * inv;
   G.ni = S((float)nis * inv);
   G.status = ST_OK;
+}
+// the record's own (float) incoming direction
+template <int PLIES = 2, class S>
+__device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
+                                         const MatVars<S>& mv, const Record& q, Geo<S>& G) {
+  geometry_k<PLIES, S, float>(m, map, mv, q, mk3<float>(q.wi[0], q.wi[1], q.wi[2]), G);
 }
 
 // ------------------------------------------------------------ microfacet --
@@ -515,8 +527,9 @@ struct Shade {
   V3<S> t, b, n, wi;
   S mui, at, ab, g, fr;
   bool at_free, ab_free;  // roughness not clamped (its derivative passes)
-  S body_x0;  // r B G / (1 + a(mu_i)): f_x^B per unit albedo before its angular term
-  S body_y0;  // (1 - r) B G / pi: f_y^B per unit albedo per unit cosine
+  S body_x0;  // G / (1 + a(mu_i)): f_x^B per unit r B k^B_x before its angular term
+  S body_y0;  // G / pi: f_y^B per unit (1 - r) B k^B_y per unit cosine
+  float ni_sy;  // N_i |x - y|: d ln tau / d sigma_t = -ni_sy
   // transmission path (f_y^S)
   bool tt_ok;
   V3<S> iy, by, ny;
@@ -530,10 +543,11 @@ __device__ __forceinline__ S clamp_alpha(const S& a) {
   return a;
 }
 
+// wi: the record's incoming direction as S (seeded for direction tangents)
 template <class S>
 __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
-                                           const Geo<S>& G, const Record& q, Shade<S>& s) {
-  s.wi = lift3<S>(q.wi[0], q.wi[1], q.wi[2]);
+                                           const Geo<S>& G, const V3<S>& wi, Shade<S>& s) {
+  s.wi = wi;
   s.n = G.n;
   s.t = G.t;
   s.b = cross(s.n, s.t);
@@ -556,9 +570,10 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   s.body_x0 = S(0.f);
   if (vf(s.mui) > 0.f) {
     const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + S(1.f) / s.mui));
-    s.body_x0 = (m.r * m.B) * s.g / (1.0f + aLS);
+    s.body_x0 = s.g / (1.0f + aLS);
   }
-  s.body_y0 = ((1.0f - m.r) * m.B * (1.0f / kPi)) * s.g;
+  s.body_y0 = s.g * (1.0f / kPi);
+  s.ni_sy = 0.f;
   s.tt_ok = false;
   // Sec. 4.1.1 (reading): smooth refraction into the yarn at x, straight path
   // to the yarn surface y, attenuation tau^{N_i} (Eq. 4)
@@ -578,15 +593,25 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   s.by = mk3<S>(s.ny.y, -s.ny.x, S(0.f));  // n_y x z
   s.iy = -din;
   s.tau = xexp(-(m.sigma_t * G.ni * sy));
+  s.ni_sy = vf(G.ni) * vf(sy);
   s.tx = 1.0f - s.fr;
   s.tt_ok = true;
 }
+template <class S>
+__device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
+                                           const Geo<S>& G, const Record& q, Shade<S>& s) {
+  make_shade(m, mv, G, lift3<S>(q.wi[0], q.wi[1], q.wi[2]), s);
+}
 
 // f |wo.n| of the four lobes at wo; spec = f_x^S + f_y^S (grey), body = the
-// body lobes per unit albedo; pdf terms of the four sampling strategies.
+// body lobe per unit colour (k^B_x if refl, else k^B_y); pdf terms of the four
+// sampling strategies.  spec_u = spec / k^S and body_w = body / (r B) (refl)
+// or body / ((1 - r) B) carry the closed-form derivatives in k_spec, B, r.
 template <class S>
 struct LobeVals {
   S spec, body, pR, pT, pxb, pyb;
+  S spec_u, body_w;
+  bool refl;
 };
 
 template <class S>
@@ -619,16 +644,22 @@ __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, c
   L.pT = S(0.f);
   L.pxb = S(0.f);
   L.pyb = S(0.f);
+  L.spec_u = S(0.f);
+  L.body_w = S(0.f);
+  L.refl = true;
   if (!(vf(s.mui) > 0.f)) return;
   const S muo = dot(wo, s.n);
   const bool refl = vf(muo) > 0.f;
+  L.refl = refl;
   if (!refl && !(vf(muo) < 0.f)) return;
-  // Eqs. 5-6: body lobes, per unit albedo
+  // Eqs. 5-6: body lobes, per unit colour
   if (refl) {
-    L.body = s.body_x0 * (S(1.0f / (4.0f * kPi)) / (s.mui + muo) + 1.0f / kPi) * muo;
+    L.body_w = s.body_x0 * (S(1.0f / (4.0f * kPi)) / (s.mui + muo) + 1.0f / kPi) * muo;
+    L.body = (m.r * m.B) * L.body_w;
     L.pxb = muo * (1.0f / kPi);
   } else {
-    L.body = s.body_y0 * (-muo);
+    L.body_w = s.body_y0 * (-muo);
+    L.body = ((1.0f - m.r) * m.B) * L.body_w;
     L.pyb = -muo * (1.0f / kPi);
   }
   // Eq. 2 (reflection at x, Walter et al. 2007 with GGX) and Eq. 3 (exit BTDF
@@ -671,14 +702,15 @@ __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, c
   const S F = fresnel(refl ? ih : -ih, refl ? m.eta : m.inv_eta);
   if (refl) {
     const S q = g1i * D / (4.0f * s.mui);
-    L.spec = m.ks * F * g1o * q;
+    L.spec_u = F * g1o * q;
     L.pR = q;
   } else {
     const S den = m.eta * ih + oh;
     const S q = g1i * (-ih) * D * oh / ((-ion) * den * den);
-    L.spec = m.ks * s.tx * s.tau * (1.0f - F) * g1o * q;
+    L.spec_u = s.tx * s.tau * (1.0f - F) * g1o * q;
     L.pT = q;
   }
+  L.spec = m.ks * L.spec_u;
 }
 
 // Sec. 4.1.5: lobe probabilities (1 - B) F(mu_i), (1 - B)(1 - F), B r, B (1 - r).

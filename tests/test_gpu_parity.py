@@ -175,6 +175,132 @@ def test_backward_matches_oracle_gradient(orc, api, sorted_mode):
             api.eval_backward(M, d, gt, deterministic=True)
 
 
+def _ext_materials():
+    # the paper's fitting set varied per material; half of them with a
+    # separate transmission body colour k^B_y
+    mats = I.materials(5)[:12]
+    rng = np.random.default_rng(71)
+    for k, d in enumerate(mats):
+        d["body_r"] = float(rng.uniform(0.2, 0.8))
+        d["body_B"] = float(rng.uniform(0.3, 0.8))
+        d["sigma_t"] = float(rng.uniform(0.2, 1.5))
+        d["k_spec"] = float(rng.uniform(0.5, 1.0))
+        if k % 2:
+            d["albedo_y"] = [float(x) for x in rng.uniform(0.1, 0.9, 3)]
+    return mats
+
+
+@pytest.mark.parametrize("sorted_mode", [False, True])
+def test_extended_backward_matches_oracle(orc, api, sorted_mode):
+    mats = _ext_materials()
+    n = 6007
+    rec = I.random_records(n, n_mat=12, seed=53, wi_mode="cosine", sorted_ids=True, v_max=20.0)
+    rec["ratio"] = np.where(np.arange(n) % 3 == 0, 0.4, 0.0).astype(np.float32)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 12) if sorted_mode else None
+    g = np.random.default_rng(54).uniform(-1, 1, (3, n)).astype(np.float32)
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, rec)
+    good = PU.stable_mask([fb], [(q[0],) for q in pert], sb, [q[2] for q in pert])
+    g[:, ~good] = 0.0
+    grad_o, gwi_o, gwo_o, _, J = orc.grad_ext_records(mats, rec, g.astype(np.float64),
+                                                      threads=8, jac=True)
+    scale = np.zeros((12, 15))
+    np.add.at(scale, rec["mat_id"], np.abs(g.T[:, :, None] * J[:, :, :15]).sum(1))
+    M = api.Materials(mats)
+    d = dev(api, rec, seg)
+    gt = torch.from_numpy(g).cuda()
+    gp, gwi, gwo = api.eval_backward_ext(M, d, gt, dirs=True)
+    gp, gwi, gwo = np_(gp), np_(gwi), np_(gwo)
+    PU.dump(f"ext_bwd_{int(sorted_mode)}", gp=gp, gwi=gwi, gwo=gwo, grad_o=grad_o, gwi_o=gwi_o,
+            gwo_o=gwo_o, scale=scale, good=good)
+    err = np.abs(gp - grad_o)
+    assert (err <= 1e-4 * scale + 1e-6).all(), (err / (scale + 1e-12)).max(axis=0)
+    # per-record direction products: the scale of each is sum_c |g_c| |df_c/dw|
+    for got, ref, lo in ((gwi, gwi_o, 15), (gwo, gwo_o, 18)):
+        sc = np.einsum("ck,kcd->dk", np.abs(g), np.abs(J[:, :, lo:lo + 3]))
+        ok = np.abs(got - ref) <= 1e-3 * sc + 1e-5
+        share = ok[:, good].all(axis=0).mean()
+        assert share >= 0.99, share
+        assert np.all(got[:, sb != 0] == 0)
+    # the 8-parameter call: albedo moves both body colours (tied materials)
+    g8 = np_(api.eval_backward(M, d, gt))
+    tied = np.array([("albedo_y" not in m) for m in mats])
+    np.testing.assert_allclose(g8[tied, 0:3], (gp[:, 0:3] + gp[:, 9:12])[tied], rtol=1e-4,
+                               atol=1e-5)
+    np.testing.assert_allclose(g8[:, 3:8], gp[:, 3:8], rtol=1e-4, atol=1e-5)
+    if sorted_mode:
+        a, _, _ = api.eval_backward_ext(M, d, gt, deterministic=True)
+        b, _, _ = api.eval_backward_ext(M, d, gt, deterministic=True)
+        assert np.array_equal(np_(a), np_(b))
+        assert (np.abs(np_(a) - grad_o) <= 1e-4 * scale + 1e-6).all()
+
+
+def test_extended_params_round_trip(api):
+    mats = _ext_materials()[:4]
+    M = api.Materials(mats)
+    p15 = api.default_params_ext(mats).cuda()
+    np.testing.assert_allclose(np_(M.get_params_ext()), np_(p15), rtol=1e-6, atol=1e-7)
+    q = p15.clone()
+    q[:, 8] = 0.3
+    q[:, 9:12] = 0.25
+    q[:, 12:15] = torch.tensor([0.9, 0.45, 0.8])
+    M.set_params_ext(q)
+    np.testing.assert_allclose(np_(M.get_params_ext()), np_(q), rtol=1e-6, atol=1e-7)
+    # the 8-column call ties k^B_y to the albedo and keeps the rest
+    p8 = q[:, :8].clone()
+    p8[:, 0:3] = 0.6
+    M.set_params(p8)
+    back = np_(M.get_params_ext())
+    np.testing.assert_allclose(back[:, 9:12], 0.6, rtol=1e-6)
+    np.testing.assert_allclose(back[:, 12:15], np_(q[:, 12:15]), rtol=1e-6)
+    np.testing.assert_allclose(np_(M.get_params()), np_(p8), rtol=1e-6)
+
+
+def test_extended_fitting_of_the_papers_parameter_set(orc, api):
+    # Sec. 5.2 fits r, k^B_x, k^B_y and sigma_t to a target: here the target
+    # is the oracle at held-out values, the start 20% off
+    mats = _ext_materials()[:4]
+    for d in mats:
+        d.setdefault("albedo_y", [0.5, 0.4, 0.3])
+    n = 4096
+    rec = I.random_records(n, n_mat=4, seed=63, wi_mode="cosine", sorted_ids=True, v_max=5.0)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 4)
+    M = api.Materials(mats)
+    d = dev(api, rec, seg)
+    theta_star = api.default_params_ext(mats).cuda()
+    tgt, _, st_t = orc.eval_records(mats, rec, threads=8)
+    target = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    mask = torch.from_numpy(st_t == 0).cuda()
+    free = [0, 1, 2, 8, 9, 10, 11, 12]
+    g = torch.Generator().manual_seed(64)
+    start = theta_star.cpu()[:, free] * (1 + 0.2 * (2 * torch.rand(4, len(free), generator=g) - 1))
+    x = start.cuda().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=0.005)
+    wi = d["wi"].clone()
+    wo = d["wo"].clone()
+    losses = []
+    for _ in range(100):
+        p = theta_star.clone()
+        p[:, free] = x
+        f, st = api.bysdf_ext(p, wi, wo, M, d)
+        loss = ((f - target) ** 2 * mask).sum() / mask.sum()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    # directions as differentiable inputs: autograd returns the library's
+    # per-record products
+    wi_r = d["wi"].clone().requires_grad_(True)
+    wo_r = d["wo"].clone().requires_grad_(True)
+    f, _ = api.bysdf_ext(theta_star, wi_r, wo_r, M, d)
+    gsum = torch.ones_like(f)
+    f.backward(gsum)
+    _, gwi, gwo = api.eval_backward_ext(M, d, gsum, dirs=True)
+    np.testing.assert_array_equal(np_(wi_r.grad), np_(gwi))
+    np.testing.assert_array_equal(np_(wo_r.grad), np_(gwo))
+
+
 def test_autograd_function_and_fitting(orc, api):
     mats = I.materials(5)[:4]
     n = 4096

@@ -12,9 +12,12 @@ tests under ``tests/test_oracle_*.py`` (closed forms, brute force, invariants).
 from .oracle import (  # noqa: F401
     NPARAM,
     NPARAM_EXT,
+    STOCH_JITTER_NODES,
+    STOCH_ROUGH_ENTRY,
     build,
     count_ops,
     eval_records,
+    eval_stochastic_records,
     fiber_map,
     fiber_map_tab,
     fresnel,
@@ -28,8 +31,11 @@ from .oracle import (  # noqa: F401
     lobes,
     btdf,
     pdf_records,
+    philox4x64,
     ply_occlusion,
     sample_records,
+    sample_stochastic_records,
+    stoch_nodes,
     vndf_pdf,
     vndf_sample,
 )

@@ -379,6 +379,56 @@ bool valid_rec(const Rec& q, int n_mat, bool need_wo, bool need_u) {
   return true;
 }
 
+// ------------------------------------------------------------- randomness --
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC 2011): ten rounds of two 64x64 -> 128-bit multiplies
+// of the counter words, key bumped by the Weyl constants between rounds.
+struct Philox4x64 {
+  uint64_t w[4];
+};
+Philox4x64 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                      uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  uint64_t c[4] = {c0, c1, c2, c3};
+  for (int r = 0; r < 10; ++r) {
+    const unsigned __int128 p0 = (unsigned __int128)M0 * c[0];
+    const unsigned __int128 p1 = (unsigned __int128)M1 * c[2];
+    const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  return Philox4x64{{c[0], c[1], c[2], c[3]}};
+}
+// 24 high bits of a word as a float in [0, 1)
+double unit24(uint64_t w) { return (double)(w >> 40) * (1.0 / 16777216.0); }
+
+// Stochastic estimators (Sec. 4.2 stratified h nodes; Eq. 1's Omega_y
+// integral with a GGX-sampled refraction).  Record index `index`: node j's
+// jitter is word j % 4 of the block with counter (index, j / 4, 0, 0); the
+// entry microfacet takes words 0 and 1 of block (index, 16, 0, 0); key
+// (seed, ORC_STOCH_KEY1).
+struct Stoch {
+  bool jitter = false, rough = false;
+  uint64_t seed = 0;
+  uint64_t index = 0;
+  double xi(int j) const {
+    const Philox4x64 r = philox4x64(index, (uint64_t)(j / 4), 0, 0, seed, ORC_STOCH_KEY1);
+    return unit24(r.w[j % 4]);
+  }
+  void entry(double* v0, double* v1) const {
+    const Philox4x64 r = philox4x64(index, 16, 0, 0, seed, ORC_STOCH_KEY1);
+    *v0 = unit24(r.w[0]);
+    *v1 = unit24(r.w[1]);
+  }
+};
+
 // --------------------------------------------------------------- geometry --
 // One node of the implicit geometry: the camera ray entering the yarn at
 // in-plane point X0 with in-plane unit direction e and longitudinal slope
@@ -564,7 +614,7 @@ struct Geo {
 // averaged (normal, tangent, shadowing, hit point, N_i), nodes without a ply
 // hit are dropped.  K = 1 at h0 is the near field (Sec. 4.1).
 template <class S>
-Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi) {
+Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi, const Stoch* sc = nullptr) {
   using std::sqrt;
   const MatStatic& st = *m.st;
   Geo<S> G;
@@ -580,7 +630,9 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi) {
   S gs = S(0.0), nis = S(0.0);
   const int K = G.fp.K;
   for (int j = 0; j < K; ++j) {
-    const double hj = (double)G.fp.h1 + ((j + 0.5) * (double)G.fp.width) / K;
+    // midpoint of stratum j, or a uniform point in it (stratified jitter)
+    const double xj = (sc && sc->jitter) ? sc->xi(j) : 0.5;
+    const double hj = (double)G.fp.h1 + ((j + xj) * (double)G.fp.width) / K;
     const double uj = (q.u - g0) + std::asin(hj);
     const double X0x = st.L.R * std::cos(uj), X0y = st.L.R * std::sin(uj);
     Node<S> nd = node_geometry(m, X0x, X0y, ex, ey, q.v, kappa, wi);
@@ -609,8 +661,8 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi) {
   return G;
 }
 template <class S>
-Geo<S> geometry(const Mat<S>& m, const Rec& q) {
-  return geometry(m, q, lift<S>(q.wi));
+Geo<S> geometry(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
+  return geometry(m, q, lift<S>(q.wi), sc);
 }
 
 // -------------------------------------------------------------- microfacet --
@@ -693,7 +745,8 @@ S clamp_alpha(const S& a) {
 }
 
 template <class S>
-Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi) {
+Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi,
+                    const Stoch* sc = nullptr) {
   using std::exp;
   using std::sqrt;
   const orc_material& d = m.st->d;
@@ -726,10 +779,24 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi) {
   // Sec. 4.1.1, reading: the camera ray refracts smoothly into the yarn at x
   // (transmittance 1 - F), travels straight to the yarn surface y, and is
   // attenuated by tau^{N_i} (Eq. 4).
-  const S s2t = (1.0 - s.mui * s.mui) / (d.eta * d.eta);
-  if (!(s.mui > 0.0) || s2t >= 1.0) return s;
+  // Rough entry (Eq. 1, the Omega_y integral, reading): the refracting
+  // normal is a GGX visible normal m about n instead of n itself; the entry
+  // transmittance is 1 - F(omega_i . m); a ray refracted outward carries no
+  // transmission.
+  V3<S> mn = s.n;
+  S ci = s.mui;
+  if (sc && sc->rough && s.mui > 0.0) {
+    double v0, v1;
+    sc->entry(&v0, &v1);
+    const V3<S> ml = vndf_sample(to_local(s.wi, s.t, s.b, s.n), s.at, s.ab, v0, v1);
+    mn = s.t * ml.x + s.b * ml.y + s.n * ml.z;
+    ci = dot(s.wi, mn);
+  }
+  const S s2t = (1.0 - ci * ci) / (d.eta * d.eta);
+  if (!(s.mui > 0.0) || !(ci > 0.0) || s2t >= 1.0) return s;
   const S cost = sqrt(1.0 - s2t);
-  const V3<S> din = s.wi * (-1.0 / d.eta) + s.n * (s.mui / d.eta - cost);
+  const V3<S> din = s.wi * (-1.0 / d.eta) + mn * (ci / d.eta - cost);
+  if (!(dot(din, s.n) < 0.0)) return s;
   const S a = din.x * din.x + din.y * din.y;
   if (!(a > 1e-12)) return s;
   const S bq = G.x.x * din.x + G.x.y * din.y;
@@ -745,7 +812,7 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi) {
   s.iy = -din;
   s.path = sy;
   s.tau = exp(-(m.sigma_t * G.ni * sy));
-  s.tx = 1.0 - s.fr;
+  s.tx = 1.0 - ((sc && sc->rough) ? fresnel(ci, d.eta) : s.fr);
   s.tt_ok = true;
   return s;
 }
@@ -855,29 +922,30 @@ struct Out {
 // wi, wo: the record's directions as scalars of type S (seeded for
 // derivatives with respect to them)
 template <class S>
-Out<S> eval_one(const Mat<S>& m, const Rec& q, const V3<S>& wi, const V3<S>& wo) {
+Out<S> eval_one(const Mat<S>& m, const Rec& q, const V3<S>& wi, const V3<S>& wo,
+                const Stoch* sc = nullptr) {
   Out<S> o;
-  const Geo<S> G = geometry(m, q, wi);
+  const Geo<S> G = geometry(m, q, wi, sc);
   if (G.status != ORC_OK) {
     o.status = ORC_NO_HIT;
     return o;
   }
-  const Shade<S> s = make_shade(m, G, wi);
+  const Shade<S> s = make_shade(m, G, wi, sc);
   const Lobes<S> L = eval_lobes(s, wo);
   total(s, L, o.f, &o.pdf);
   o.status = ORC_OK;
   return o;
 }
 template <class S>
-Out<S> eval_one(const Mat<S>& m, const Rec& q) {
-  return eval_one(m, q, lift<S>(q.wi), lift<S>(q.wo));
+Out<S> eval_one(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
+  return eval_one(m, q, lift<S>(q.wi), lift<S>(q.wo), sc);
 }
 
 template <class S>
-Out<S> sample_one(const Mat<S>& m, const Rec& q) {
+Out<S> sample_one(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
   using std::sqrt;
   Out<S> o;
-  const Geo<S> G = geometry(m, q);
+  const Geo<S> G = geometry(m, q, sc);
   if (G.status != ORC_OK) {
     // Reading: no ply hit is a pass-through, a delta in direction -omega_i.
     o.status = ORC_NO_HIT;
@@ -887,7 +955,7 @@ Out<S> sample_one(const Mat<S>& m, const Rec& q) {
     }
     return o;
   }
-  const Shade<S> s = make_shade(m, G, q.wi);
+  const Shade<S> s = make_shade(m, G, lift<S>(q.wi), sc);
   double P[4];
   lobe_probs(s, P);
   // Sec. 4.1.5: one random number picks the lobe and is rescaled for reuse.
@@ -1127,6 +1195,76 @@ int orc_grad_ext(const orc_material* m, int n_mat, const orc_records* r, int64_t
     grad[k] = s;
   }
   return 0;
+}
+
+int orc_eval_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                        uint64_t seed, int64_t index_offset, uint32_t flags, double* f_rgb,
+                        double* pdf, uint8_t* status, int n_threads) {
+  Batch B = make_batch(m, n_mat);
+  if (!B.ok) return -1;
+  parallel_for(n, n_threads, [&](int64_t b, int64_t e, int) {
+    std::vector<Mat<double>> mats;
+    for (auto& st : B.st) mats.push_back(make_mat<double>(st, false));
+    Stoch sc;
+    sc.jitter = (flags & ORC_STOCH_JITTER_NODES) != 0;
+    sc.rough = (flags & ORC_STOCH_ROUGH_ENTRY) != 0;
+    sc.seed = seed;
+    for (int64_t i = b; i < e; ++i) {
+      const Rec q = read_rec(r, i, n);
+      sc.index = (uint64_t)(index_offset + i);
+      Out<double> o;
+      if (valid_rec(q, n_mat, true, false)) o = eval_one(mats[q.mat], q, &sc);
+      for (int c = 0; c < 3; ++c) f_rgb[c * n + i] = o.f[c];
+      if (pdf) pdf[i] = o.pdf;
+      status[i] = (uint8_t)o.status;
+    }
+  });
+  return 0;
+}
+
+int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                          uint64_t seed, int64_t index_offset, uint32_t flags, double* wo,
+                          double* weight, double* pdf, uint8_t* lobe_status, int n_threads) {
+  Batch B = make_batch(m, n_mat);
+  if (!B.ok) return -1;
+  parallel_for(n, n_threads, [&](int64_t b, int64_t e, int) {
+    std::vector<Mat<double>> mats;
+    for (auto& st : B.st) mats.push_back(make_mat<double>(st, false));
+    Stoch sc;
+    sc.jitter = (flags & ORC_STOCH_JITTER_NODES) != 0;
+    sc.rough = (flags & ORC_STOCH_ROUGH_ENTRY) != 0;
+    sc.seed = seed;
+    for (int64_t i = b; i < e; ++i) {
+      const Rec q = read_rec(r, i, n);
+      sc.index = (uint64_t)(index_offset + i);
+      Out<double> o;
+      if (valid_rec(q, n_mat, false, true)) o = sample_one(mats[q.mat], q, &sc);
+      for (int c = 0; c < 3; ++c) {
+        wo[c * n + i] = o.wo[c];
+        weight[c * n + i] = o.weight[c];
+      }
+      pdf[i] = o.pdf;
+      lobe_status[i] = (uint8_t)(o.status | (o.lobe << 4));
+    }
+  });
+  return 0;
+}
+
+int orc_stoch_nodes(double h0, int has_ratio, double ratio, int k_max, uint64_t seed,
+                    uint64_t index, double* h_out) {
+  const Footprint fp = footprint(h0, has_ratio != 0, ratio, k_max);
+  Stoch sc;
+  sc.jitter = true;
+  sc.seed = seed;
+  sc.index = index;
+  for (int j = 0; j < fp.K; ++j)
+    h_out[j] = (double)fp.h1 + ((j + sc.xi(j)) * (double)fp.width) / fp.K;
+  return fp.K;
+}
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  const Philox4x64 r = philox4x64(ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1]);
+  for (int k = 0; k < 4; ++k) out[k] = r.w[k];
 }
 
 int orc_count_ops(const orc_material* m, int n_mat, const orc_records* r,

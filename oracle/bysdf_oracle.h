@@ -96,6 +96,29 @@ int orc_grad(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
 int orc_grad_ext(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
                  const double* g_rgb, double* grad, double* g_wi, double* g_wo,
                  double* jac, double* f_rgb, int n_threads);
+/* Stochastic estimators of the paper's integrals, with random numbers from
+ * Philox4x64-10 (Salmon et al. 2011) keyed by (seed, ORC_STOCH_KEY1) and
+ * counted by the record's global index index_offset + i:
+ *   ORC_STOCH_JITTER_NODES: the K footprint nodes at uniform points of their
+ *     strata (Sec. 4.2, stratified sampling of h) instead of the midpoints;
+ *     node j uses word j % 4 of counter (index, j / 4, 0, 0);
+ *   ORC_STOCH_ROUGH_ENTRY: the entry refraction through a GGX visible normal
+ *     (one sample of Eq. 1's Omega_y integral), words 0, 1 of (index, 16, 0, 0).
+ * Outputs as orc_eval / orc_sample. */
+#define ORC_STOCH_JITTER_NODES 1u
+#define ORC_STOCH_ROUGH_ENTRY 2u
+#define ORC_STOCH_KEY1 0xB15DF0005EED0001ull
+int orc_eval_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                        uint64_t seed, int64_t index_offset, uint32_t flags, double* f_rgb,
+                        double* pdf, uint8_t* status, int n_threads);
+int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
+                          uint64_t seed, int64_t index_offset, uint32_t flags, double* wo,
+                          double* weight, double* pdf, uint8_t* lobe_status, int n_threads);
+/* The jittered node positions h_j of one record (returns K; h_out[K]). */
+int orc_stoch_nodes(double h0, int has_ratio, double ratio, int k_max, uint64_t seed,
+                    uint64_t index, double* h_out);
+/* One Philox4x64-10 block (the generator behind the stochastic estimators). */
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 /* Operation counts of one evaluation per record.  op: 0 eval (with pdf),
  * 1 sample, 3 the geometry and shading state that eval and sample share.
  * counts: [n][6] = add/sub, mul, div, sqrt, transcendental, compare. */

@@ -108,6 +108,14 @@ def lib():
         L.orc_sample.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, C.c_int]
         L.orc_grad.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, C.c_int]
         L.orc_grad_ext.argtypes = [MP, C.c_int, RP, C.c_int64, P, P, P, P, P, P, C.c_int]
+        L.orc_eval_stochastic.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_uint64, C.c_int64,
+                                          C.c_uint32, P, P, P, C.c_int]
+        L.orc_sample_stochastic.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_uint64, C.c_int64,
+                                            C.c_uint32, P, P, P, P, C.c_int]
+        L.orc_stoch_nodes.argtypes = [C.c_double, C.c_int, C.c_double, C.c_int, C.c_uint64,
+                                      C.c_uint64, P]
+        L.orc_philox4x64.argtypes = [P, P, P]
+        L.orc_philox4x64.restype = None
         L.orc_count_ops.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_int, P]
         L.orc_geometry.argtypes = [MP, C.c_float, C.c_float, C.c_float, P, C.c_float,
                                    C.POINTER(Geo)]
@@ -258,6 +266,52 @@ def grad_ext_records(mats, rec, g_rgb, threads: int = 1, jac: bool = False):
                           None if J is None else J.ctypes.data, f.ctypes.data, threads):
         raise ValueError("oracle: bad material description")
     return (grad, gwi, gwo, f, J) if jac else (grad, gwi, gwo, f)
+
+
+STOCH_JITTER_NODES, STOCH_ROUGH_ENTRY = 1, 2
+
+
+def eval_stochastic_records(mats, rec, seed: int, flags: int, index_offset: int = 0,
+                            threads: int = 1):
+    """Stochastic estimators (jittered nodes, rough entry): f, pdf, status."""
+    keep = []
+    M = _materials(mats)
+    r, n = _records(rec, keep)
+    f = np.zeros((3, n)); pdf = np.zeros(n); st = np.zeros(n, np.uint8)
+    if lib().orc_eval_stochastic(M, len(mats), C.byref(r), n, seed, index_offset, flags,
+                                 f.ctypes.data, pdf.ctypes.data, st.ctypes.data, threads):
+        raise ValueError("oracle: bad material description")
+    return f, pdf, st
+
+
+def sample_stochastic_records(mats, rec, seed: int, flags: int, index_offset: int = 0,
+                              threads: int = 1):
+    keep = []
+    M = _materials(mats)
+    rec = dict(rec); rec.pop("wo", None)
+    r, n = _records(rec, keep)
+    wo = np.zeros((3, n)); w = np.zeros((3, n)); pdf = np.zeros(n)
+    ls = np.zeros(n, np.uint8)
+    if lib().orc_sample_stochastic(M, len(mats), C.byref(r), n, seed, index_offset, flags,
+                                   wo.ctypes.data, w.ctypes.data, pdf.ctypes.data,
+                                   ls.ctypes.data, threads):
+        raise ValueError("oracle: bad material description")
+    return wo, w, pdf, ls & 15, ls >> 4
+
+
+def stoch_nodes(h0, ratio, k_max, seed, index):
+    out = np.zeros(64)
+    K = lib().orc_stoch_nodes(float(np.float32(h0)), 1, float(np.float32(ratio)), k_max,
+                              seed, index, out.ctypes.data)
+    return out[:K]
+
+
+def philox4x64(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, np.uint64)
+    lib().orc_philox4x64(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
 
 
 def count_ops(mats, rec, op: int = 0):

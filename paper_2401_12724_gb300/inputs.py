@@ -13,7 +13,7 @@ and parameter ranges of five benchmark workloads:
   4  256 materials, Zipf(1.1) record counts totalling 2^26, material-sorted
   5  64 materials, 2^24 material-sorted records, upstream gradients (fitting)
 
-Random numbers come from NumPy's Philox-4x32-10 (a counter-based generator),
+Random numbers come from NumPy's Philox-4x64-10 (a counter-based generator),
 keyed by (seed, workload); records are drawn in chunks of 2^16 so that any
 sub-range is reproducible on its own.
 """

@@ -470,8 +470,12 @@ def other_workloads(api, N, torch, args, sm_count):
     n = int(d["h"].shape[0])
     o = api.alloc_fused(n, "cuda")
     ms, _ = timed(lambda: api.eval_sample_pdf(M, d, out=o), steps, 2)
+    # the stochastic estimators (jittered nodes + GGX-sampled entry)
+    ms_st, _ = timed(lambda: api.eval_sample_pdf_stochastic(M, d, 1, 3, out=o),
+                     max(3, steps // 4), 2)
     res[I.WORKLOAD_NAME[3]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
-                                   roofline_frac=frac(OPS[3]["fused"], n, ms, sm_count))
+                                   roofline_frac=frac(OPS[3]["fused"], n, ms, sm_count),
+                                   stochastic_records_per_s=n / (ms_st / 1e3))
     del d, o
     torch.cuda.empty_cache()
     # batched heterogeneous: 256 materials, Zipf counts, one persistent

@@ -207,6 +207,45 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
                           uint8_t* lobe_status_s, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/* Stochastic estimators of the paper's integrals, as options of eval and the
+ * fused op (the deterministic calls above take midpoints and the smooth
+ * entry):
+ *   BYSDF_STOCH_JITTER_NODES: the K footprint nodes at uniform points of
+ *     their strata of [h1, h2] (Sec. 4.2: stratified Monte Carlo sampling of
+ *     h) instead of the midpoints; the near field (no footprint) is unchanged;
+ *   BYSDF_STOCH_ROUGH_ENTRY: one sample of the Omega_y integral of Eq. 1: the
+ *     camera ray refracts into the yarn through a GGX visible normal m at x
+ *     (roughness of the shading point) instead of n; the entry transmittance
+ *     is 1 - F(omega_i . m); a ray refracted outward gives no transmission.
+ * Random numbers: Philox4x64-10 (Salmon et al. 2011), key (seed,
+ * 0xB15DF0005EED0001), counter (index_offset + i, block, 0, 0) for record i:
+ * node j uses word j % 4 of block j / 4; the entry microfacet words 0 and 1
+ * of block 16; a word w gives (w >> 40) * 2^-24.  The same seed and index
+ * draw the same nodes and entry in eval and in the fused op, so a sample's
+ * pdf is the stochastic eval's pdf at the sampled direction.  Launches use
+ * the op's configured block and items at occupancy 0.  Other arguments and
+ * errors as bysdf_eval / bysdf_eval_sample_pdf; NULL options: BYSDF_E_ARG;
+ * unknown flag bits: BYSDF_E_ARG. */
+#define BYSDF_STOCH_JITTER_NODES 1u
+#define BYSDF_STOCH_ROUGH_ENTRY 2u
+typedef struct bysdf_stochastic {
+  uint64_t seed;         /* generator key word 0 */
+  int64_t index_offset;  /* global index of record 0 (e.g. a shard's first) */
+  uint32_t flags;        /* BYSDF_STOCH_* bits; 0 = the deterministic estimate */
+  uint32_t reserved;     /* 0 */
+} bysdf_stochastic;
+
+int bysdf_eval_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
+                          const bysdf_stochastic* options, int64_t n, float* f_rgb, float* pdf,
+                          uint8_t* status, void* workspace, size_t workspace_bytes,
+                          void* stream);
+int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
+                                     const bysdf_stochastic* options, const float* u0,
+                                     const float* u1, int64_t n, float* f_rgb, float* pdf,
+                                     uint8_t* status, float* wo_s, float* weight_s,
+                                     float* pdf_s, uint8_t* lobe_status_s, void* workspace,
+                                     size_t workspace_bytes, void* stream);
+
 /* Gradient of sum_i sum_c grad_f[c][i] * f_c(record i) with respect to the 8
  * parameters of each material (layout of bysdf_set_params), accumulated
  * into grad_params[n_mat][8] (DEVICE, zeroed by this call).  The forward pass

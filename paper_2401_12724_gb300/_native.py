@@ -40,6 +40,13 @@ class Outputs(C.Structure):
                 ("lobe_status", C.c_void_p), ("grad_params", C.c_void_p)]
 
 
+class Stochastic(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("index_offset", C.c_int64), ("flags", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+STOCH_JITTER_NODES, STOCH_ROUGH_ENTRY = 1, 2
+
 # (name, restype, argtypes) of every symbol declared in include/bysdf.h
 P = C.c_void_p
 SYMBOLS = [
@@ -58,6 +65,11 @@ SYMBOLS = [
     ("bysdf_pdf", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, P, C.c_size_t, P]),
     ("bysdf_eval_sample_pdf", C.c_int,
      [P, C.POINTER(Hits), P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_size_t, P]),
+    ("bysdf_eval_stochastic", C.c_int,
+     [P, C.POINTER(Hits), C.POINTER(Stochastic), C.c_int64, P, P, P, P, C.c_size_t, P]),
+    ("bysdf_eval_sample_pdf_stochastic", C.c_int,
+     [P, C.POINTER(Hits), C.POINTER(Stochastic), P, P, C.c_int64, P, P, P, P, P, P, P, P,
+      C.c_size_t, P]),
     ("bysdf_eval_backward", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_eval_backward_ext", C.c_int,
      [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_int, P, C.c_size_t, P]),

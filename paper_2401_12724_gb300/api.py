@@ -225,6 +225,39 @@ def eval_sample_pdf(mats: Materials, rec: dict, u0=None, u1=None, stream=None, o
     return o
 
 
+def eval_stochastic(mats: Materials, rec: dict, seed: int, flags: int, index_offset: int = 0,
+                    with_pdf: bool = True, stream=None, out=None):
+    """The stochastic estimators (N.STOCH_* flags): f, pdf, status as eval."""
+    n = _n(rec)
+    dev = rec["h"].device
+    f = out["f"] if out else _empty((3, n), torch.float32, dev)
+    pdf = (out["pdf"] if out else _empty((n,), torch.float32, dev)) if with_pdf else None
+    st = out["status"] if out else _empty((n,), torch.uint8, dev)
+    opt = N.Stochastic(int(seed), int(index_offset), int(flags), 0)
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_stochastic(mats.handle, C.byref(hits_struct(rec)), C.byref(opt),
+                                           n, _ptr(f), _ptr(pdf), _ptr(st), _ptr(ws), ws.numel(),
+                                           _stream(stream)), "bysdf_eval_stochastic")
+    return f, pdf, st
+
+
+def eval_sample_pdf_stochastic(mats: Materials, rec: dict, seed: int, flags: int,
+                               index_offset: int = 0, u0=None, u1=None, stream=None,
+                               out=None) -> dict:
+    n = _n(rec)
+    o = out if out is not None else alloc_fused(n, rec["h"].device)
+    u0 = rec["u0"] if u0 is None else u0
+    u1 = rec["u1"] if u1 is None else u1
+    opt = N.Stochastic(int(seed), int(index_offset), int(flags), 0)
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_sample_pdf_stochastic(
+        mats.handle, C.byref(hits_struct(rec)), C.byref(opt), _ptr(u0), _ptr(u1), n,
+        _ptr(o["f"]), _ptr(o["pdf"]), _ptr(o["status"]), _ptr(o["wo"]), _ptr(o["weight"]),
+        _ptr(o["pdf_s"]), _ptr(o["lobe_status"]), _ptr(ws), ws.numel(), _stream(stream)),
+        "bysdf_eval_sample_pdf_stochastic")
+    return o
+
+
 def eval_backward(mats: Materials, rec: dict, grad_f: torch.Tensor, deterministic: bool = False,
                   stream=None, out=None) -> torch.Tensor:
     """d(sum grad_f * f) / d params, shape (n_mat, 8)."""

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libbysdf.so")
 SOURCES = ["bysdf_api.cu", "bysdf_fwd.cu", "bysdf_fwd_eval.cu", "bysdf_fwd_sample.cu",
-           "bysdf_fwd_pdf.cu", "bysdf_fwd_fused.cu", "bysdf_bwd.cu"]
+           "bysdf_fwd_pdf.cu", "bysdf_fwd_fused.cu", "bysdf_fwd_stoch.cu", "bysdf_bwd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -23,7 +23,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompil
 # backward kernel keeps IEEE-rounded ones for its derivatives.
 FAST_FLAGS = {s: ["-prec-div=false", "-prec-sqrt=false"]
               for s in ("bysdf_fwd_eval.cu", "bysdf_fwd_sample.cu", "bysdf_fwd_pdf.cu",
-                        "bysdf_fwd_fused.cu", "bysdf_fwd.cu")}
+                        "bysdf_fwd_fused.cu", "bysdf_fwd_stoch.cu", "bysdf_fwd.cu")}
 _lock = threading.Lock()
 
 

@@ -370,10 +370,21 @@ int op_bits(int op) {
   return 0;
 }
 
+// sto: the stochastic estimators (flags != 0), eval and fused ops only
 int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const float* u0,
                 const float* u1, int64_t n, const bysdf_outputs& o, void* ws, size_t ws_bytes,
-                cudaStream_t st, const bysdf_launch_config& c, size_t ws_need = 0) {
-  const int bits = op_bits(op);
+                cudaStream_t st, const bysdf_launch_config& cfg, size_t ws_need = 0,
+                const bysdf_stochastic* sto = nullptr) {
+  int bits = op_bits(op);
+  bysdf_launch_config c = cfg;
+  if (sto && sto->flags) {
+    if (sto->flags & ~(uint32_t)(BYSDF_STOCH_JITTER_NODES | BYSDF_STOCH_ROUGH_ENTRY))
+      return fail(BYSDF_E_ARG, "unknown stochastic flags");
+    if (op != BYSDF_OP_EVAL && op != BYSDF_OP_FUSED)
+      return fail(BYSDF_E_UNSUPPORTED, "stochastic estimators: eval and the fused op only");
+    bits |= OPF_STOCH;
+    c.occupancy = 0;  // instantiated in the 128-register shapes
+  }
   const bool need_wo = (bits & (OPF_EVAL | OPF_PDF)) != 0;
   int rc = check_hits(m, h, need_wo, n);
   if (rc) return rc;
@@ -407,6 +418,11 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   a.weight_s = o.weight;
   a.pdf_s = o.pdf_s;
   a.lstat_s = o.lobe_status;
+  if (bits & OPF_STOCH) {
+    a.stoch_seed = sto->seed;
+    a.stoch_index0 = sto->index_offset;
+    a.stoch_flags = sto->flags;
+  }
   const size_t smem = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
                                               : (size_t)(c.block / 32) * m->stride;
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
@@ -914,6 +930,40 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_FUSED, hits, u0, u1, n, o, workspace, workspace_bytes,
                      reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED]);
+}
+
+int bysdf_eval_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
+                          const bysdf_stochastic* sto, int64_t n, float* f_rgb, float* pdf,
+                          uint8_t* status, void* workspace, size_t workspace_bytes,
+                          void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  if (!sto) return fail(BYSDF_E_ARG, "stochastic options are NULL");
+  bysdf_outputs o{};
+  o.f_rgb = f_rgb;
+  o.pdf = pdf;
+  o.status = status;
+  return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_EVAL], 0, sto);
+}
+
+int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
+                                     const bysdf_stochastic* sto, const float* u0,
+                                     const float* u1, int64_t n, float* f_rgb, float* pdf,
+                                     uint8_t* status, float* wo_s, float* weight_s,
+                                     float* pdf_s, uint8_t* lobe_status_s, void* workspace,
+                                     size_t workspace_bytes, void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  if (!sto) return fail(BYSDF_E_ARG, "stochastic options are NULL");
+  bysdf_outputs o{};
+  o.f_rgb = f_rgb;
+  o.pdf = pdf;
+  o.status = status;
+  o.wo = wo_s;
+  o.weight = weight_s;
+  o.pdf_s = pdf_s;
+  o.lobe_status = lobe_status_s;
+  return run_forward(m, BYSDF_OP_FUSED, hits, u0, u1, n, o, workspace, workspace_bytes,
+                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED], 0, sto);
 }
 
 int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,

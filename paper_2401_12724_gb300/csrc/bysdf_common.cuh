@@ -44,6 +44,46 @@ __host__ __device__ inline size_t mat_stride_bytes(int t_max) {
 // through GGX D and Smith G1) are differentiated in closed form.
 enum { D_ALPHA_P = 0, D_ALPHA_F = 1, ND = 2 };
 
+// ------------------------------------------------------------- randomness --
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of two
+// 64 x 64 -> 128-bit products of the counter words, the key bumped by the
+// Weyl constants between rounds.  Drives the stochastic estimators.
+struct U64x4 {
+  uint64_t w[4];
+};
+__device__ __forceinline__ U64x4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                            uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  return U64x4{{c0, c1, c2, c3}};
+}
+// 24 high bits of a word as a float in [0, 1) (exact)
+__device__ __forceinline__ float unit24(uint64_t w) {
+  return (float)(uint32_t)(w >> 40) * (1.0f / 16777216.0f);
+}
+// key word 1 of the stochastic estimators' generator
+constexpr uint64_t kStochKey1 = 0xB15DF0005EED0001ull;
+enum : uint32_t { STOCH_JITTER_NODES = 1u, STOCH_ROUGH_ENTRY = 2u };
+// Per record: node j's jitter is word j % 4 of counter (index, j / 4, 0, 0);
+// the entry microfacet takes words 0, 1 of (index, 16, 0, 0); key (seed,
+// kStochKey1).
+struct StochCtx {
+  uint32_t flags;
+  uint64_t seed, index;
+};
+
 // ------------------------------------------------------------ dual numbers --
 template <int N>
 struct DualF {

@@ -7,7 +7,8 @@
 
 namespace bysdf {
 
-enum : int { OPF_EVAL = 1, OPF_SAMPLE = 2, OPF_PDF = 4 };
+// OPF_STOCH: the stochastic estimators (jittered nodes, GGX-sampled entry)
+enum : int { OPF_EVAL = 1, OPF_SAMPLE = 2, OPF_PDF = 4, OPF_STOCH = 8 };
 enum : int { MODE_ALL_SMEM = 0, MODE_SORTED = 1 };
 enum : uint32_t { ERR_TABLE_WAIT = 1u, ERR_TABLE_INFLIGHT = 2u };
 
@@ -41,6 +42,10 @@ struct KArgs {
   int32_t n_param;       // gradient columns: 8, or 15 (extended set)
   int32_t pad_np;
   float *grad_wi, *grad_wo;  // direction backward: 3 planes each, or NULL
+  uint64_t stoch_seed;       // stochastic estimators: generator key word 0,
+  int64_t stoch_index0;      //   global index of record 0,
+  uint32_t stoch_flags;      //   STOCH_* bits
+  uint32_t pad_st;
   WsCtl* ctl;
   const int32_t* tile_start;
 };
@@ -138,9 +143,17 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
   Shade<float> s;
   if (eval_ok || samp_ok) {
     const MatVars<float> mv = mat_vars<float>(m);
-    geometry<PLIES>(m, map, mv, q, G);
-    st = G.status;
-    if (st == ST_OK) make_shade(m, mv, G, q, s);
+    if constexpr ((OP & OPF_STOCH) != 0) {
+      const StochCtx sc{a.stoch_flags, a.stoch_seed, (uint64_t)(a.stoch_index0 + i)};
+      const V3<float> wi = mk3<float>(q.wi[0], q.wi[1], q.wi[2]);
+      geometry_k<PLIES, float, float>(m, map, mv, q, wi, G, &sc);
+      st = G.status;
+      if (st == ST_OK) make_shade(m, mv, G, wi, s, &sc);
+    } else {
+      geometry<PLIES>(m, map, mv, q, G);
+      st = G.status;
+      if (st == ST_OK) make_shade(m, mv, G, q, s);
+    }
   }
   if constexpr (kEval) {
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, p = 0.f;

@@ -378,10 +378,12 @@ struct Geo {
 
 // PLIES: plies traced side by side in the float pass of the ply trace (2
 // gives each lane two independent dependency chains and costs ~5 registers)
+// sc: the stochastic estimators' state (jittered nodes), or NULL
 template <int PLIES = 2, class S, class K>
 __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
                                            const MatVars<S>& mv, const Record& q,
-                                           const V3<K>& wi, Geo<S>& G) {
+                                           const V3<K>& wi, Geo<S>& G,
+                                           const StochCtx* sc = nullptr) {
   G.status = ST_NO_HIT;
   const Footprint fp = footprint(q.h, q.ratio, m.kmax);
   G.width = fp.width;
@@ -415,12 +417,21 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   float dgs = 0.f;
   int nis = 0, nhit = 0;
   const bool near = fp.K == 1 && fp.width == 0.0f;
+  const bool jitter = sc != nullptr && (sc->flags & STOCH_JITTER_NODES) != 0;
+  U64x4 rnd = {{0, 0, 0, 0}};
   for (int j = 0; j < fp.K; ++j) {
     float X0x, X0y;
     if (near) {
       sincosf(q.u, &X0y, &X0x);
     } else {
-      const float hj = fp.h1 + ((float)j + 0.5f) * fp.width / (float)fp.K;
+      // midpoint of stratum j, or a uniform point in it (Sec. 4.2, stratified
+      // sampling of h)
+      float xj = 0.5f;
+      if (jitter) {
+        if ((j & 3) == 0) rnd = philox4x64(sc->index, (uint64_t)(j >> 2), 0, 0, sc->seed, kStochKey1);
+        xj = unit24(rnd.w[j & 3]);
+      }
+      const float hj = fp.h1 + ((float)j + xj) * fp.width / (float)fp.K;
       sincosf(u_rel + asinf(hj), &X0y, &X0x);
     }
     X0x *= m.R;
@@ -543,10 +554,12 @@ __device__ __forceinline__ S clamp_alpha(const S& a) {
   return a;
 }
 
-// wi: the record's incoming direction as S (seeded for direction tangents)
+// wi: the record's incoming direction as S (seeded for direction tangents);
+// sc: the stochastic estimators' state (GGX-sampled entry), or NULL
 template <class S>
 __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
-                                           const Geo<S>& G, const V3<S>& wi, Shade<S>& s) {
+                                           const Geo<S>& G, const V3<S>& wi, Shade<S>& s,
+                                           const StochCtx* sc = nullptr) {
   s.wi = wi;
   s.n = G.n;
   s.t = G.t;
@@ -577,10 +590,26 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   s.tt_ok = false;
   // Sec. 4.1.1 (reading): smooth refraction into the yarn at x, straight path
   // to the yarn surface y, attenuation tau^{N_i} (Eq. 4)
-  const S s2t = (1.0f - s.mui * s.mui) * (m.inv_eta * m.inv_eta);
-  if (!(vf(s.mui) > 0.f) || !(vf(s2t) < 1.0f)) return;
+  // Rough entry (Eq. 1's Omega_y integral, one sample): the refracting normal
+  // is a GGX visible normal m about n; the entry transmittance is
+  // 1 - F(omega_i . m); a ray refracted outward carries no transmission
+  V3<S> mn = s.n;
+  S ci = s.mui;
+  const bool rough = sc != nullptr && (sc->flags & STOCH_ROUGH_ENTRY) != 0;
+  if (rough && vf(s.mui) > 0.f) {
+    const U64x4 rnd = philox4x64(sc->index, 16, 0, 0, sc->seed, kStochKey1);
+    const float v0 = unit24(rnd.w[0]), v1 = unit24(rnd.w[1]);
+    float sphi, cphi;
+    sincospif(2.0f * v1, &sphi, &cphi);
+    const V3<S> ml = vndf_sample(to_local(s.wi, s.t, s.b, s.n), s.at, s.ab, sqrtf(v0), sphi, cphi);
+    mn = s.t * ml.x + s.b * ml.y + s.n * ml.z;
+    ci = dot(s.wi, mn);
+  }
+  const S s2t = (1.0f - ci * ci) * (m.inv_eta * m.inv_eta);
+  if (!(vf(s.mui) > 0.f) || !(vf(ci) > 0.f) || !(vf(s2t) < 1.0f)) return;
   const S ct = xsqrt(1.0f - s2t);
-  const V3<S> din = s.wi * (-m.inv_eta) + s.n * (s.mui * m.inv_eta - ct);
+  const V3<S> din = s.wi * (-m.inv_eta) + mn * (ci * m.inv_eta - ct);
+  if (rough && !(vf(dot(din, s.n)) < 0.f)) return;
   const S a = din.x * din.x + din.y * din.y;
   if (!(vf(a) > 1e-12f)) return;
   const S bq = G.x.x * din.x + G.x.y * din.y;
@@ -594,7 +623,7 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   s.iy = -din;
   s.tau = xexp(-(m.sigma_t * G.ni * sy));
   s.ni_sy = vf(G.ni) * vf(sy);
-  s.tx = 1.0f - s.fr;
+  s.tx = 1.0f - (rough ? fresnel(ci, m.eta) : s.fr);
   s.tt_ok = true;
 }
 template <class S>

@@ -301,6 +301,68 @@ def test_extended_fitting_of_the_papers_parameter_set(orc, api):
     np.testing.assert_array_equal(np_(wo_r.grad), np_(gwo))
 
 
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_stochastic_estimators_match_oracle(orc, api, flags):
+    # multi-scale records (jittered nodes act on footprints), the same seed
+    # and global indices on both sides
+    mats = I.materials(3)
+    rec = I.records(3, 0, 8009)
+    seed, off = 20240607, 11
+    M = api.Materials(mats)
+    d = dev(api, rec)
+    f, p, st = (np_(t) for t in api.eval_stochastic(M, d, seed, flags, index_offset=off))
+    PU.dump(f"stoch_{flags}", f=f, p=p, st=st, **{"rec_" + k: v for k, v in rec.items()})
+    fn = lambda r: orc.eval_stochastic_records(mats, r, seed, flags, index_offset=off,  # noqa
+                                                threads=8)
+    (fb, pb, sb), pert = PU.conditioning(fn, rec)
+    PU.assert_status(st, sb, [q[2] for q in pert], f"stoch{flags}")
+    PU.assert_parity(f, fb, [q[0] for q in pert], f"stoch{flags}.f")
+    PU.assert_parity(p, pb, [q[1] for q in pert], f"stoch{flags}.pdf")
+    # the estimate moved away from the deterministic one
+    f_det = np_(api.eval(M, d)[0])
+    assert (np.abs(f - f_det) > 1e-3 * (np.abs(f_det) + 1e-3)).any(axis=0).mean() > 0.05
+    # the fused op draws the same nodes and entry: its eval part is the
+    # stochastic eval, its sample matches the oracle's stochastic sample
+    o = api.eval_sample_pdf_stochastic(M, d, seed, flags, index_offset=off)
+    fo = np_(o["f"])
+    PU.assert_parity(fo, fb, [q[0] for q in pert], f"stoch{flags}.fused_f")
+    # another instantiation rounds differently: agreement with the eval call
+    # up to float32 rounding except at steep spots
+    assert np.isclose(fo, f, rtol=1e-5, atol=1e-7).all(axis=0).mean() >= 0.999
+    fn_s = lambda r: orc.sample_stochastic_records(mats, r, seed, flags,  # noqa: E731
+                                                    index_offset=off, threads=8)
+    base, pert = PU.conditioning(fn_s, rec, sample=True)
+    wob, wb, pb_s, sb_s, lb = base
+    wo, w, ps, ls = np_(o["wo"]), np_(o["weight"]), np_(o["pdf_s"]), np_(o["lobe_status"])
+    PU.assert_status(ls, sb_s | (lb << 4), [q[3] | (q[4] << 4) for q in pert], "stoch.ls")
+    both_ok = (sb_s == 0) & ((ls & 15) == 0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ang = np.where(both_ok, PU.angle_between(wo, wob), 0.0)
+    PU.assert_parity(wo, wob, [q[0] for q in pert], "stoch.wo", err=ang / PU.ANGLE)
+    PU.assert_parity(w, wb, [q[1] for q in pert], "stoch.weight")
+    PU.assert_parity(ps, pb_s, [q[2] for q in pert], "stoch.pdf_s")
+
+
+def test_stochastic_options_and_sharding(api):
+    mats = I.materials(3)
+    rec = I.records(3, 0, 6001)
+    M = api.Materials(mats)
+    d = dev(api, rec)
+    # no flags: the deterministic kernels, bit for bit
+    f0, p0, s0 = (np_(t) for t in api.eval(M, d))
+    f1, p1, s1 = (np_(t) for t in api.eval_stochastic(M, d, 5, 0))
+    assert np.array_equal(f0, f1) and np.array_equal(p0, p1) and np.array_equal(s0, s1)
+    # a shard with its global index offset reproduces its part of the batch
+    full = np_(api.eval_stochastic(M, d, 77, 3)[0])
+    k = 2500
+    part = {kk: (v[..., k:].contiguous() if v.shape[-1] == 6001 else v) for kk, v in d.items()}
+    shard = np_(api.eval_stochastic(M, part, 77, 3, index_offset=k)[0])
+    assert np.array_equal(shard, full[:, k:])
+    # unknown flag bits are refused
+    with pytest.raises(RuntimeError, match="flags"):
+        api.eval_stochastic(M, d, 1, 8)
+
+
 def test_autograd_function_and_fitting(orc, api):
     mats = I.materials(5)[:4]
     n = 4096

@@ -29,6 +29,8 @@ from .oracle import (  # noqa: F401
     layout,
     lib,
     lobes,
+    migration_info,
+    migration_texels,
     btdf,
     pdf_records,
     philox4x64,

@@ -258,21 +258,53 @@ struct MatStatic {
   orc_material d;
   Layout L;
   std::vector<double> tab_delta, tab_of;
+  // fiber migration: layouts and maps of the sunk rings k = 1 .. K_m - 1
+  // (index 0 repeats the regular ring's)
+  std::vector<Layout> Lm;
+  std::vector<std::vector<double>> mig_delta, mig_of;
 };
+
+// Map k of a migrating ply (reading): the outer ring sunk by k r_f / K_m,
+// holding as many fibers as fit on it.
+Layout migration_layout(const Layout& L, int k, int K) {
+  Layout Lk = L;
+  Lk.Rfc = L.Rfc - k * L.rf / K;
+  Lk.ok = L.rf < Lk.Rfc;
+  if (Lk.ok) Lk.M = (int)std::ceil(PI / std::asin(L.rf / Lk.Rfc));
+  return Lk;
+}
+
+void tabulate(const Layout& L, int T, bool flat, std::vector<double>& dl,
+              std::vector<double>& of) {
+  dl.assign(T, 0.0);
+  of.assign(T, 0.0);
+  if (flat) return;
+  for (int i = 0; i < T; ++i) {
+    const double D = ((i + 0.5) / T - 0.5) * 2.0 * PI / L.M;
+    dl[i] = fiber_delta(L, D);
+    of[i] = fiber_occlusion(L, D);
+  }
+}
 
 bool build_static(const orc_material& d, MatStatic& st) {
   st.d = d;
   st.L = make_layout(d);
   if (!st.L.ok) return false;
   const int T = d.map_texels;
-  st.tab_delta.assign(T, 0.0);
-  st.tab_of.assign(T, 0.0);
-  if (!(d.flags & 1)) {
-    for (int i = 0; i < T; ++i) {
-      const double D = ((i + 0.5) / T - 0.5) * 2.0 * PI / st.L.M;
-      st.tab_delta[i] = fiber_delta(st.L, D);
-      st.tab_of[i] = fiber_occlusion(st.L, D);
-    }
+  const bool flat = (d.flags & 1) != 0;
+  tabulate(st.L, T, flat, st.tab_delta, st.tab_of);
+  const int K = d.migration_maps;
+  if (K < 1 || K > 4) return false;
+  if (K > 1 && !(d.migration_length > 0.0 && std::isfinite(d.migration_length) &&
+                 d.migration_blend > 0.0 && d.migration_blend <= 0.5))
+    return false;
+  st.Lm.assign(K, st.L);
+  st.mig_delta.assign(K, st.tab_delta);
+  st.mig_of.assign(K, st.tab_of);
+  for (int k = 1; k < K; ++k) {
+    st.Lm[k] = migration_layout(st.L, k, K);
+    if (!st.Lm[k].ok) return false;
+    tabulate(st.Lm[k], T, flat, st.mig_delta[k], st.mig_of[k]);
   }
   return true;
 }
@@ -285,6 +317,7 @@ struct Mat {
   // Sec. 4.1.3 / 4.1.5 weights and Eq. 4 attenuation (the paper's fitting set)
   S body_r, body_B, sigma_t, k_spec;
   S alb_y[3];  // k^B_y of Eq. 6 (equal to alb unless the material sets it)
+  S omega_fm[4];  // fiber phase rates of the migration maps' rings
 };
 
 template <class S> void seed(S&, int) {}
@@ -330,6 +363,7 @@ Mat<S> make_mat(const MatStatic& st, bool with_tangents, bool ext = false) {
   // ply sits on the axis and does not wind (Sec. 3.4).
   m.omega_p = d.n_plies == 1 ? S(0.0) : tan(m.alpha_p) / st.L.Rc;
   m.omega_f = tan(m.alpha_f) / st.L.Rfc;
+  for (size_t k = 0; k < st.Lm.size(); ++k) m.omega_fm[k] = tan(m.alpha_f) / st.Lm[k].Rfc;
   return m;
 }
 
@@ -447,17 +481,22 @@ struct Node {
 // Sec. 3.5.1: periodic linear interpolation of a map tabulated at texel
 // centres; theta_f is the fiber phase (radians), one period is 2 pi / M.
 template <class S>
-void fiber_lookup(const MatStatic& st, const S& theta_f, S* delta, S* of) {
+void fiber_lookup_tab(const MatStatic& st, int Mk, const std::vector<double>& tab_delta,
+                      const std::vector<double>& tab_of, const S& theta_f, S* delta, S* of) {
   const int T = st.d.map_texels;
-  const S w = theta_f * (st.L.M / (2.0 * PI));
+  const S w = theta_f * (Mk / (2.0 * PI));
   const S a = w + 0.5 - std::floor(val(w + 0.5));
   const S tau = a * (double)T - 0.5;
   const double fl = std::floor(val(tau));
   const S f = tau - fl;
   const int i0 = (((int)fl) % T + T) % T;
   const int i1 = (i0 + 1) % T;
-  *delta = (1.0 - f) * st.tab_delta[i0] + f * st.tab_delta[i1];
-  *of = (1.0 - f) * st.tab_of[i0] + f * st.tab_of[i1];
+  *delta = (1.0 - f) * tab_delta[i0] + f * tab_delta[i1];
+  *of = (1.0 - f) * tab_of[i0] + f * tab_of[i1];
+}
+template <class S>
+void fiber_lookup(const MatStatic& st, const S& theta_f, S* delta, S* of) {
+  fiber_lookup_tab(st, st.L.M, st.tab_delta, st.tab_of, theta_f, delta, of);
 }
 
 // Sec. 4.1.4 (ply shadowing), reading: occlusion of x on ply k by the other
@@ -488,6 +527,52 @@ S ply_occlusion(const Mat<S>& m, int k, const S& psi_k, const S& xx, const S& xy
     }
   }
   return occ / (2.0 * L.Rp);
+}
+
+// Sec. 3.5 fiber migration (reading): the map of segment `seg` along the yarn
+int migration_map(const MatStatic& st, int64_t seg) {
+  const Philox4x64 r = philox4x64((uint64_t)seg, 0, 0, 0,
+                                  (uint64_t)(uint32_t)st.d.migration_seed, ORC_MIG_KEY1);
+  return (int)(r.w[0] % (uint64_t)st.d.migration_maps);
+}
+
+// delta and o_f at ply azimuth u_ply and height z of a migrating ply: the
+// segment's map, blended linearly with the neighbour's within the blend
+// fraction of the segment length from a boundary (weight 1/2 at the
+// boundary, so the maps switch continuously)
+template <class S>
+void migration_lookup(const Mat<S>& m, const S& u_ply, const S& z, S* delta, S* of) {
+  using std::floor;
+  const MatStatic& st = *m.st;
+  const double L = st.d.migration_length, b = st.d.migration_blend;
+  const S q = z / L;
+  const double sf = std::floor(val(q));
+  const S t = q - sf;
+  const int64_t seg = (int64_t)sf;
+  S w = S(0.0);
+  int64_t nb = seg;
+  if (val(t) < b) {
+    w = 0.5 - t / (2.0 * b);
+    nb = seg - 1;
+  } else if (val(t) > 1.0 - b) {
+    w = 0.5 - (1.0 - t) / (2.0 * b);
+    nb = seg + 1;
+  }
+  const int k0 = migration_map(st, seg);
+  S d0, o0;
+  fiber_lookup_tab(st, st.Lm[k0].M, st.mig_delta[k0], st.mig_of[k0],
+                   u_ply - m.omega_fm[k0] * z, &d0, &o0);
+  if (!(val(w) > 0.0)) {
+    *delta = d0;
+    *of = o0;
+    return;
+  }
+  const int k1 = migration_map(st, nb);
+  S d1, o1;
+  fiber_lookup_tab(st, st.Lm[k1].M, st.mig_delta[k1], st.mig_of[k1],
+                   u_ply - m.omega_fm[k1] * z, &d1, &o1);
+  *delta = (1.0 - w) * d0 + w * d1;
+  *of = (1.0 - w) * o0 + w * o1;
 }
 
 template <class S>
@@ -560,7 +645,10 @@ Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
   const S ecx = cos(best_psi), ecy = sin(best_psi);
   g.u_ply = atan2(ecx * g.np.y - ecy * g.np.x, ecx * g.np.x + ecy * g.np.y);
   const S theta_f = g.u_ply - m.omega_f * zx;
-  fiber_lookup(st, theta_f, &g.delta, &g.of);
+  if (st.d.migration_maps > 1)
+    migration_lookup(m, g.u_ply, zx, &g.delta, &g.of);
+  else
+    fiber_lookup(st, theta_f, &g.delta, &g.of);
   // n_f = n'(R(n_p)), t_f = t'(R(t_p)): R tilts the tangent by the fiber
   // helix angle about n_p; n' tilts the normal by delta about t_f.
   g.tf = g.tp * cos(m.alpha_f) + ep * sin(m.alpha_f);
@@ -1347,6 +1435,27 @@ int orc_layout(const orc_material* m, double* out) {
   out[4] = st.L.M;
   out[5] = mat.omega_p;
   out[6] = mat.omega_f;
+  return 0;
+}
+
+int orc_migration_info(const orc_material* m, int k, int64_t seg, double* out) {
+  MatStatic st;
+  if (!build_static(*m, st)) return -1;
+  if (k < 0 || k >= (int)st.Lm.size()) return -1;
+  out[0] = st.Lm[k].Rfc;
+  out[1] = st.Lm[k].M;
+  out[2] = st.d.migration_maps > 1 ? migration_map(st, seg) : 0;
+  return 0;
+}
+
+int orc_migration_texels(const orc_material* m, int k, double* delta, double* of) {
+  MatStatic st;
+  if (!build_static(*m, st)) return -1;
+  if (k < 0 || k >= (int)st.Lm.size()) return -1;
+  for (int t = 0; t < st.d.map_texels; ++t) {
+    delta[t] = st.mig_delta[k][t];
+    of[t] = st.mig_of[k][t];
+  }
   return 0;
 }
 

@@ -43,6 +43,16 @@ typedef struct orc_material {
   double packing;          /* fiber area fraction of a ply cross-section */
   double albedo_y[3];      /* k^B_y (RGB) of the transmission body lobe (Eq. 6);
                               negative: equal to albedo */
+  /* Fiber migration (Sec. 3.5, reading): migration_maps K_m in [1, 4] 1D map
+   * pairs; map 0 is the regular outer ring, map k >= 1 the ring sunk by
+   * k r_f / K_m (fewer fibers fit).  The yarn is cut into segments of
+   * migration_length along v; segment s uses map (Philox word of s) mod K_m
+   * and blends linearly with its neighbour within migration_blend (in (0,
+   * 0.5]) of the length from each boundary.  K_m = 1: no migration. */
+  int32_t migration_maps;
+  int32_t migration_seed;
+  double migration_length;
+  double migration_blend;
 } orc_material;
 
 /* Structure-of-arrays hit records; wi/wo are [3][n] planes (x, y, z). */
@@ -108,6 +118,7 @@ int orc_grad_ext(const orc_material* m, int n_mat, const orc_records* r, int64_t
 #define ORC_STOCH_JITTER_NODES 1u
 #define ORC_STOCH_ROUGH_ENTRY 2u
 #define ORC_STOCH_KEY1 0xB15DF0005EED0001ull
+#define ORC_MIG_KEY1 0xB15DF000F1BE0002ull /* key word 1 of the migration map choice */
 int orc_eval_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
                         uint64_t seed, int64_t index_offset, uint32_t flags, double* f_rgb,
                         double* pdf, uint8_t* status, int n_threads);
@@ -117,6 +128,10 @@ int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r
 /* The jittered node positions h_j of one record (returns K; h_out[K]). */
 int orc_stoch_nodes(double h0, int has_ratio, double ratio, int k_max, uint64_t seed,
                     uint64_t index, double* h_out);
+/* Fiber migration introspection: ring radius and fiber count of map k and the
+ * map index of segment seg (out[3]); the T texels (delta, o_f) of map k. */
+int orc_migration_info(const orc_material* m, int k, int64_t seg, double* out);
+int orc_migration_texels(const orc_material* m, int k, double* delta, double* of);
 /* One Philox4x64-10 block (the generator behind the stochastic estimators). */
 void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
 /* Operation counts of one evaluation per record.  op: 0 eval (with pdf),

@@ -39,6 +39,10 @@ class Material(C.Structure):
         ("shadow_density", C.c_double),
         ("packing", C.c_double),
         ("albedo_y", C.c_double * 3),
+        ("migration_maps", C.c_int32),
+        ("migration_seed", C.c_int32),
+        ("migration_length", C.c_double),
+        ("migration_blend", C.c_double),
     ]
 
 
@@ -115,6 +119,8 @@ def lib():
         L.orc_stoch_nodes.argtypes = [C.c_double, C.c_int, C.c_double, C.c_int, C.c_uint64,
                                       C.c_uint64, P]
         L.orc_philox4x64.argtypes = [P, P, P]
+        L.orc_migration_info.argtypes = [MP, C.c_int, C.c_int64, P]
+        L.orc_migration_texels.argtypes = [MP, C.c_int, P, P]
         L.orc_philox4x64.restype = None
         L.orc_count_ops.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_int, P]
         L.orc_geometry.argtypes = [MP, C.c_float, C.c_float, C.c_float, P, C.c_float,
@@ -168,6 +174,10 @@ def _material(d: dict) -> Material:
     ay = d.get("albedo_y")
     for c in range(3):
         m.albedo_y[c] = -1.0 if ay is None else float(np.float32(ay[c]))
+    m.migration_maps = int(d.get("migration_maps", 1))
+    m.migration_seed = int(d.get("migration_seed", 0))
+    m.migration_length = float(np.float32(d.get("migration_length", 1.0)))
+    m.migration_blend = float(np.float32(d.get("migration_blend", 0.25)))
     return m
 
 
@@ -304,6 +314,21 @@ def stoch_nodes(h0, ratio, k_max, seed, index):
     K = lib().orc_stoch_nodes(float(np.float32(h0)), 1, float(np.float32(ratio)), k_max,
                               seed, index, out.ctypes.data)
     return out[:K]
+
+
+def migration_info(mat, k: int, seg: int = 0):
+    out = np.zeros(3)
+    if lib().orc_migration_info(C.byref(_material(mat)), k, seg, out.ctypes.data):
+        raise ValueError("oracle: bad material description or map index")
+    return dict(Rfc=out[0], M=int(out[1]), map_of_segment=int(out[2]))
+
+
+def migration_texels(mat, k: int):
+    T = int(mat["map_texels"])
+    dl = np.zeros(T); of = np.zeros(T)
+    if lib().orc_migration_texels(C.byref(_material(mat)), k, dl.ctypes.data, of.ctypes.data):
+        raise ValueError("oracle: bad material description or map index")
+    return dl, of
 
 
 def philox4x64(ctr, key):

@@ -297,6 +297,10 @@ def _material_f64(O):
                     m.beta_deg[c] = float(d["beta_deg"][c])
             elif f == "flags":
                 m.flags = int(d.get("flags", 0))
+            elif f.startswith("migration_"):
+                dflt = dict(migration_maps=1, migration_seed=0, migration_length=1.0,
+                            migration_blend=0.25)[f]
+                setattr(m, f, type(dflt)(d.get(f, dflt)))
             else:
                 setattr(m, f, d[f] if t.__name__.startswith("c_int") else float(d[f]))
         return m

@@ -478,6 +478,22 @@ def other_workloads(api, N, torch, args, sm_count):
                                    stochastic_records_per_s=n / (ms_st / 1e3))
     del d, o
     torch.cuda.empty_cache()
+    # fiber migration (Sec. 3.5): the workload-2 records and materials, each
+    # material with 2 map pairs switched along the yarn (tables still fit in
+    # shared memory)
+    mats = I.materials(2)
+    for k, dsc in enumerate(mats):
+        dsc.update(migration_maps=2, migration_seed=k, migration_length=0.5,
+                   migration_blend=0.25)
+    M = api.Materials(mats)
+    _, d, _ = workload_device(api, 2, 0)
+    n = int(d["h"].shape[0])
+    o = api.alloc_fused(n, "cuda")
+    ms, _ = timed(lambda: api.eval_sample_pdf(M, d, out=o), max(3, steps // 2), 2)
+    res["migration-2maps-" + I.WORKLOAD_NAME[2]] = dict(records_per_s=n / (ms / 1e3), ms=ms,
+                                                        records=n)
+    del d, o
+    torch.cuda.empty_cache()
     # batched heterogeneous: 256 materials, Zipf counts, one persistent
     # material-sorted launch per op captured in a CUDA graph, vs plain
     mats = I.materials(4)

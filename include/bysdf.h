@@ -89,6 +89,19 @@ typedef struct bysdf_material_desc {
   float albedo_y[3];      /* k^B_y (RGB) of the transmission body lobe, Eq. 6;
                              negative: equal to albedo (one body colour for
                              both lobes, the default reading)               */
+  /* Fiber migration (Sec. 3.5, reading): K_m = migration_maps in [1, 4] map
+   * pairs; map 0 is the regular outer ring, map k >= 1 the ring sunk by
+   * k r_f / K_m (as many fibers as fit on it).  The yarn is cut into
+   * segments of migration_length along v; segment s uses map
+   * (word 0 of Philox4x64-10 with counter (s, 0, 0, 0) and key
+   * (migration_seed, 0xB15DF000F1BE0002)) mod K_m and blends linearly with
+   * its neighbour within migration_blend (in (0, 0.5]) of the length from
+   * each boundary.  K_m = 1 (or 0): no migration; the other fields are then
+   * ignored.  Each extra map adds 32 + 8 T bytes to the material's table. */
+  int32_t migration_maps;
+  int32_t migration_seed;
+  float migration_length;
+  float migration_blend;
 } bysdf_material_desc;
 
 /* Opaque material table: per-material constants and the 1D fiber normal and

@@ -529,10 +529,12 @@ S ply_occlusion(const Mat<S>& m, int k, const S& psi_k, const S& xx, const S& xy
   return occ / (2.0 * L.Rp);
 }
 
-// Sec. 3.5 fiber migration (reading): the map of segment `seg` along the yarn
+// Sec. 3.5 fiber migration (reading): the map of segment `seg` along the
+// yarn; the choice repeats every 256 segments ("periodically and randomly")
 int migration_map(const MatStatic& st, int64_t seg) {
-  const Philox4x64 r = philox4x64((uint64_t)seg, 0, 0, 0,
-                                  (uint64_t)(uint32_t)st.d.migration_seed, ORC_MIG_KEY1);
+  const uint64_t s256 = (uint64_t)(((seg % 256) + 256) % 256);
+  const Philox4x64 r = philox4x64(s256, 0, 0, 0, (uint64_t)(uint32_t)st.d.migration_seed,
+                                  ORC_MIG_KEY1);
   return (int)(r.w[0] % (uint64_t)st.d.migration_maps);
 }
 

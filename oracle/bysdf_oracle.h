@@ -46,9 +46,11 @@ typedef struct orc_material {
   /* Fiber migration (Sec. 3.5, reading): migration_maps K_m in [1, 4] 1D map
    * pairs; map 0 is the regular outer ring, map k >= 1 the ring sunk by
    * k r_f / K_m (fewer fibers fit).  The yarn is cut into segments of
-   * migration_length along v; segment s uses map (Philox word of s) mod K_m
-   * and blends linearly with its neighbour within migration_blend (in (0,
-   * 0.5]) of the length from each boundary.  K_m = 1: no migration. */
+   * migration_length along v; segment s uses map (word 0 of Philox4x64-10
+   * with counter (s mod 256, 0, 0, 0), key (migration_seed, ORC_MIG_KEY1))
+   * mod K_m -- the choice repeats every 256 segments -- and blends linearly
+   * with its neighbour within migration_blend (in (0, 0.5]) of the length
+   * from each boundary.  K_m = 1: no migration. */
   int32_t migration_maps;
   int32_t migration_seed;
   double migration_length;

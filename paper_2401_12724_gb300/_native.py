@@ -20,6 +20,8 @@ class MaterialDesc(C.Structure):
         ("beta_deg", C.c_float * 2), ("body_B", C.c_float), ("body_r", C.c_float),
         ("sigma_t", C.c_float), ("shadow_density", C.c_float), ("packing", C.c_float),
         ("albedo_y", C.c_float * 3),
+        ("migration_maps", C.c_int32), ("migration_seed", C.c_int32),
+        ("migration_length", C.c_float), ("migration_blend", C.c_float),
     ]
 
 

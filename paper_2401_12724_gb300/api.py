@@ -50,6 +50,10 @@ def desc_struct(d: dict) -> N.MaterialDesc:
     ay = d.get("albedo_y")
     for c in range(3):
         s.albedo_y[c] = -1.0 if ay is None else float(ay[c])
+    s.migration_maps = int(d.get("migration_maps", 1))
+    s.migration_seed = int(d.get("migration_seed", 0))
+    s.migration_length = float(d.get("migration_length", 1.0))
+    s.migration_blend = float(d.get("migration_blend", 0.25))
     return s
 
 

@@ -58,6 +58,9 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 struct HostLayout {
   double R, Rp, Rc, rf, Rfc;
   int M;
+  int K;                   // migration map pairs (1: none)
+  double Rfc_m[4];         // ring radius and fiber count of each map
+  int M_m[4];
 };
 
 bool host_layout(const bysdf_material_desc& d, HostLayout* L, std::string* why) {
@@ -101,7 +104,43 @@ bool host_layout(const bysdf_material_desc& d, HostLayout* L, std::string* why) 
   L->Rfc = L->Rp - L->rf;
   if (!(L->rf < L->Rfc)) return bad("fibers too thick for the ply (raise fibers_per_ply)");
   L->M = (int)std::ceil(kPiD / std::asin(L->rf / L->Rfc));
+  // fiber migration: map k is the ring sunk by k r_f / K_m
+  L->K = d.migration_maps < 1 ? 1 : d.migration_maps;
+  if (L->K > 4) return bad("migration_maps outside [0, 4]");
+  if (L->K > 1) {
+    if (!(d.migration_length > 0.f) || !fin(d.migration_length))
+      return bad("migration_length must be > 0");
+    if (!(d.migration_blend > 0.f && d.migration_blend <= 0.5f))
+      return bad("migration_blend outside (0, 0.5]");
+  }
+  for (int k = 0; k < L->K; ++k) {
+    L->Rfc_m[k] = L->Rfc - k * L->rf / L->K;
+    if (!(L->rf < L->Rfc_m[k])) return bad("migration ring too deep for the fibers");
+    L->M_m[k] = k == 0 ? L->M : (int)std::ceil(kPiD / std::asin(L->rf / L->Rfc_m[k]));
+  }
   return true;
+}
+
+// Philox4x64-10 (Salmon et al. 2011) on the host: the segment table of the
+// fiber migration (map index of segment s = word 0 of counter (s, 0, 0, 0),
+// key (seed, 0xB15DF000F1BE0002), mod K_m).
+uint64_t philox4x64_word0(uint64_t c0, uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  uint64_t c[4] = {c0, 0, 0, 0};
+  for (int r = 0; r < 10; ++r) {
+    const unsigned __int128 p0 = (unsigned __int128)M0 * c[0];
+    const unsigned __int128 p1 = (unsigned __int128)M1 * c[2];
+    const uint64_t n0 = (uint64_t)(p1 >> 64) ^ c[1] ^ k0;
+    const uint64_t n2 = (uint64_t)(p0 >> 64) ^ c[3] ^ k1;
+    c[1] = (uint64_t)p1;
+    c[3] = (uint64_t)p0;
+    c[0] = n0;
+    c[2] = n2;
+    k0 += W0;
+    k1 += W1;
+  }
+  return c[0];
 }
 
 // ------------------------------------------------------------ fiber maps --
@@ -185,6 +224,12 @@ __host__ __device__ void derive_constants(MatDev& m, const double* p) {
   const double tf = tan(p[6]);
   split_hi_lo(tf * m.M / (two_pi * m.Rfc_d), &m.kf_hi, &m.kf_lo);
   m.dkf = (float)((1.0 + tf * tf) * m.M / (two_pi * m.Rfc_d));
+  // fiber migration maps: the same helix angle on their sunk rings
+  for (int k = 1; k < m.mig_maps; ++k) {
+    MigMap* mm = mig_map(m, k);
+    split_hi_lo(tf * mm->M / (two_pi * mm->Rfc_d), &mm->kf_hi, &mm->kf_lo);
+    mm->dkf = (float)((1.0 + tf * tf) * mm->M / (two_pi * mm->Rfc_d));
+  }
   m.cos_af = (float)cos(p[6]);
   m.sin_af = (float)sin(p[6]);
 }
@@ -558,7 +603,10 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
       return fail(BYSDF_E_ARG, "material " + std::to_string(i) + ": " + why);
     t_max = std::max(t_max, desc[i].map_texels);
   }
-  const size_t stride = mat_stride_bytes(t_max);
+  size_t stride = 0;
+  for (int i = 0; i < n; ++i)
+    stride = std::max(stride, mat_bytes(desc[i].map_texels, L[i].K));
+  stride = (stride + 15) / 16 * 16;
   std::vector<uint8_t> host(stride * n, 0);
   for (int i = 0; i < n; ++i) {
     const bysdf_material_desc& d = desc[i];
@@ -580,6 +628,27 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
     m.inv_2Rp = (float)(0.5 / L[i].Rp);
     m.m_over_2pi = (float)(L[i].M / (2.0 * kPiD));
     m.inv_np = (float)(1.0 / d.n_plies);
+    m.mig_maps = L[i].K;
+    m.mig_seed = d.migration_seed;
+    float inv_len_lo = 0.f;
+    if (L[i].K > 1) {
+      split_hi_lo(1.0 / (double)d.migration_length, &m.mig_inv_len, &inv_len_lo);
+      m.mig_blend = d.migration_blend;
+      m.mig_inv_2b = (float)(0.5 / (double)d.migration_blend);
+    }
+    for (int k = 1; k < L[i].K; ++k) {
+      MigMap* mm = mig_map(m, k);
+      mm->m_over_2pi = (float)(L[i].M_m[k] / (2.0 * kPiD));
+      mm->Rfc_d = L[i].Rfc_m[k];
+      mm->M = (float)L[i].M_m[k];
+      mm->aux = k == 1 ? inv_len_lo : 0.f;
+    }
+    if (L[i].K > 1) {
+      uint8_t* tab = const_cast<uint8_t*>(mig_table(m));
+      for (int sg = 0; sg < kMigPeriod; ++sg)
+        tab[sg] = (uint8_t)(philox4x64_word0((uint64_t)sg, (uint64_t)(uint32_t)d.migration_seed,
+                                             kMigKey1) % (uint64_t)L[i].K);
+    }
     for (int j = 0; j < kMaxPlies; ++j) {
       m.rot_c[j] = (float)std::cos(2.0 * kPiD * j / d.n_plies);
       m.rot_s[j] = (float)std::sin(2.0 * kPiD * j / d.n_plies);
@@ -601,6 +670,20 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
       }
       const double D = ((t + 0.5) / d.map_texels - 0.5) * 2.0 * kPiD / L[i].M;
       map[t] = make_float2((float)map_delta(L[i], D), (float)map_occlusion(L[i], D));
+    }
+    for (int k = 1; k < L[i].K; ++k) {
+      HostLayout Lk = L[i];
+      Lk.Rfc = L[i].Rfc_m[k];
+      Lk.M = L[i].M_m[k];
+      float2* mk = reinterpret_cast<float2*>(mig_map(m, k) + 1);
+      for (int t = 0; t < d.map_texels; ++t) {
+        if (d.flags & 1) {
+          mk[t] = make_float2(0.f, 0.f);
+          continue;
+        }
+        const double D = ((t + 0.5) / d.map_texels - 0.5) * 2.0 * kPiD / Lk.M;
+        mk[t] = make_float2((float)map_delta(Lk, D), (float)map_occlusion(Lk, D));
+      }
     }
   }
   bysdf_materials* M = new bysdf_materials();

@@ -16,7 +16,8 @@ constexpr int kMaxTexels = 1024;
 // Sec. 4.1.4: fiber self-occlusion o_f), one fiber period at texel centres.
 struct alignas(16) MatDev {
   int32_t np, M, T, nit;      // plies, outer-ring fibers, texels, trace updates
-  int32_t kmax, flags, pad0, pad1;
+  int32_t kmax, flags;
+  int32_t mig_maps, mig_seed;  // fiber migration: map pairs K_m (1 = none), seed
   float R, Rp, Rc, Rfc;       // yarn / ply radius, ply-centre radius, fiber ring radius
   float eta, inv_eta, B, r;   // refractive index, body share, body reflect share
   float ks, sigma_t, sigma_s, inv_2Rp;  // (1 - B) k_spec, extinction, shadow density
@@ -26,7 +27,8 @@ struct alignas(16) MatDev {
   float kf_hi, kf_lo;         // fiber phase rate in map periods per length, split
   float cos_af, sin_af;       // fiber helix angle
   float dkp, dkf;             // d kp / d alpha_p, d kf / d alpha_f
-  float inv_np, pad2, pad3, pad4;
+  float inv_np;
+  float mig_inv_len, mig_blend, mig_inv_2b;  // 1 / segment length (high part), b, 1 / (2 b)
   float rot_c[kMaxPlies], rot_s[kMaxPlies];  // cos, sin of 2 pi j / N_p
   double Rc_d, Rfc_d;         // layout radii in double (derived-constant updates)
   float alb_y[3];             // k^B_y, transmission body colour (Eq. 6)
@@ -34,9 +36,41 @@ struct alignas(16) MatDev {
 };
 static_assert(sizeof(MatDev) == 256, "MatDev must be 256 bytes");
 
-__host__ __device__ inline size_t mat_stride_bytes(int t_max) {
-  return sizeof(MatDev) + sizeof(float2) * (size_t)t_max;
+// Fiber migration map k >= 1 (Sec. 3.5): a 32-byte header, then T texels.
+// Map 0 is the regular ring whose constants live in MatDev.
+struct alignas(16) MigMap {
+  float m_over_2pi;     // M_k / (2 pi)
+  float kf_hi, kf_lo;   // fiber phase rate in map periods per length, split
+  float dkf;            // d kf / d alpha_f
+  double Rfc_d;         // ring radius of the sunk ring
+  float M;              // fibers on it
+  float aux;            // map 1 only: low part of 1 / segment length
+};
+static_assert(sizeof(MigMap) == 32, "MigMap must be 32 bytes");
+
+// Bytes of one material: header, map 0, K_m - 1 migration maps, and (when
+// migrating) the map index of each of 256 consecutive segments.
+constexpr int kMigPeriod = 256;
+__host__ __device__ inline size_t mat_bytes(int T, int K) {
+  return sizeof(MatDev) + sizeof(float2) * (size_t)T +
+         (size_t)(K - 1) * (sizeof(MigMap) + sizeof(float2) * (size_t)T) +
+         (K > 1 ? (size_t)kMigPeriod : 0);
 }
+__host__ __device__ inline const MigMap* mig_map(const MatDev& m, int k) {
+  const uint8_t* base = reinterpret_cast<const uint8_t*>(&m) + sizeof(MatDev) +
+                        sizeof(float2) * (size_t)m.T;
+  return reinterpret_cast<const MigMap*>(base + (size_t)(k - 1) *
+                                                    (sizeof(MigMap) + sizeof(float2) * (size_t)m.T));
+}
+__host__ __device__ inline MigMap* mig_map(MatDev& m, int k) {
+  return const_cast<MigMap*>(mig_map(static_cast<const MatDev&>(m), k));
+}
+// the segment table: map index of segment s is table[s mod 256]
+__host__ __device__ inline const uint8_t* mig_table(const MatDev& m) {
+  return reinterpret_cast<const uint8_t*>(mig_map(m, m.mig_maps));
+}
+// key word 1 of the migration map choice
+constexpr uint64_t kMigKey1 = 0xB15DF000F1BE0002ull;
 
 // Parameter slots carried by the dual numbers of the backward kernel: the two
 // helix angles, which move the whole geometry.  Albedo (linear), shadow

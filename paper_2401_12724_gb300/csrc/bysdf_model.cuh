@@ -43,6 +43,7 @@ struct MatVars {
   S cos_af, sin_af;     // fiber helix angle
   S sigma_s;            // shadow density
   S beta_t, beta_b;     // GGX roughness (radians)
+  bool seeded;          // helix-angle tangents carried (parameter backward)
 };
 
 template <class S>
@@ -57,8 +58,10 @@ __device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m, bool seed_params
   q.sigma_s = S(m.sigma_s);
   q.beta_t = S(m.beta_t);
   q.beta_b = S(m.beta_b);
+  q.seeded = false;
   if constexpr (is_dual<S>::value) {
     if (!seed_params) return q;
+    q.seeded = true;
     q.kp.d[D_ALPHA_P] = m.dkp;
     q.kf.d[D_ALPHA_F] = m.dkf;
     q.cos_af.d[D_ALPHA_F] = -m.sin_af;
@@ -155,10 +158,60 @@ __device__ __forceinline__ void fiber_lookup(const float2* map, int T, const S& 
   *of = t0.y + f * (t1.y - t0.y);
 }
 
-// One footprint node: the camera ray enters at in-plane point X0 with
-// in-plane unit direction e and longitudinal slope kappa (Sec. 3.4).
-// K: the type of the slope kappa and the shadow direction (wx, wy) -- float,
-// or S when the record's direction carries tangents
+// Sec. 3.5 fiber migration (reading): the yarn is cut into segments of
+// length L along v; segment s uses map table[s mod 256] (the host fills the
+// table from a Philox4x64-10 word per segment) and blends linearly with its
+// neighbour within b L of a boundary (weight 1/2 at the boundary).  Map
+// k >= 1 is the ring sunk by k r_f / K_m, with its own fiber count and phase
+// rate.  Picks the map and phase of the hit's segment (*mp, *wv) and, in a
+// blend zone, the neighbour's (*mp1, *wv1) with its weight *wgt (else 0).
+// u_ply: ply azimuth (radians); v: the record's height; dz: the hit's
+// height above it; w0: map 0's phase (periods).
+template <class S>
+__device__ __forceinline__ void migration_maps(const MatDev& m, const float2* map0,
+                                               const MatVars<S>& mv, const S& u_ply, float v,
+                                               const S& dz, const S& w0, const float2** mp,
+                                               S* wv, const float2** mp1, S* wv1, S* wgt) {
+  // t = frac((v + dz) / L) and the segment, with 1 / L as hi + lo and the
+  // product's rounding error recovered exactly
+  const MigMap* m1 = mig_map(m, 1);
+  const float ph = v * m.mig_inv_len;
+  const float pe = fmaf(v, m.mig_inv_len, -ph) + v * m1->aux;
+  float nf = floorf(ph);
+  S t = dz * m.mig_inv_len + ((ph - nf) + pe);
+  const float kf2 = floorf(vf(t));
+  t = t - kf2;
+  nf += kf2;
+  const int seg = (int)(((int64_t)nf % kMigPeriod + kMigPeriod) % kMigPeriod);
+  int nb = seg;
+  *wgt = S(0.f);
+  if (vf(t) < m.mig_blend) {
+    *wgt = 0.5f - t * m.mig_inv_2b;
+    nb = seg == 0 ? kMigPeriod - 1 : seg - 1;
+  } else if (vf(t) > 1.0f - m.mig_blend) {
+    *wgt = 0.5f - (1.0f - t) * m.mig_inv_2b;
+    nb = seg == kMigPeriod - 1 ? 0 : seg + 1;
+  }
+  const uint8_t* tab = mig_table(m);
+  auto pick = [&](int sg, const float2** p, S* wk) {
+    const int k = tab[sg];
+    if (k == 0) {
+      *p = map0;
+      *wk = w0;
+      return;
+    }
+    const MigMap* mk = mig_map(m, k);
+    S kf = S(mk->kf_hi + mk->kf_lo);
+    if constexpr (is_dual<S>::value) {
+      if (mv.seeded) kf.d[D_ALPHA_F] = mk->dkf;
+    }
+    *p = reinterpret_cast<const float2*>(mk + 1);
+    *wk = u_ply * mk->m_over_2pi - frac_prod_s(kf, mk->kf_hi, mk->kf_lo, v) - kf * dz;
+  };
+  pick(seg, mp, wv);
+  if (vf(*wgt) > 0.f) pick(nb, mp1, wv1);
+}
+
 template <class S, int PLIES = 2, class K = float>
 __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
                                               const MatVars<S>& mv, float X0x, float X0y,
@@ -337,8 +390,19 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   // centre's radial direction; fiber phase in map periods; 1D map lookup
   const S u_ply = xatan2(best_c * np.y - best_s * np.x, best_c * np.x + best_s * np.y);
   const S w = u_ply * m.m_over_2pi - phase_f_v - mv.kf * dz;
+  // map 0's phase, or the migration maps' (Sec. 3.5)
+  const float2* mp = map;
+  const float2* mp1 = map;
+  S wv = w, wv1 = w, wgt = S(0.f);
+  if (m.mig_maps > 1) migration_maps(m, map, mv, u_ply, v, dz, w, &mp, &wv, &mp1, &wv1, &wgt);
   S delta, of;
-  fiber_lookup(map, m.T, w, &delta, &of);
+  fiber_lookup(mp, m.T, wv, &delta, &of);
+  if (vf(wgt) > 0.f) {
+    S d1, o1;
+    fiber_lookup(mp1, m.T, wv1, &d1, &o1);
+    delta = delta + wgt * (d1 - delta);
+    of = of + wgt * (o1 - of);
+  }
   // n_f = n'(R(n_p)), t_f = t'(R(t_p))
   out.tf = tp * mv.cos_af + ep * mv.sin_af;
   S sd, cd;

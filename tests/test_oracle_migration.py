@@ -3,7 +3,8 @@
 Reading: a migrating ply carries K_m map pairs; map 0 is the regular outer
 ring, map k >= 1 the ring sunk by k r_f / K_m (holding as many fibers as fit
 there).  Segments of `migration_length` along the yarn pick a map by a
-Philox4x64-10 word; maps blend linearly near segment boundaries.
+Philox4x64-10 word of the segment index mod 256; maps blend linearly near
+segment boundaries.
 """
 import math
 
@@ -29,8 +30,8 @@ def mig(**kw):
 
 
 def numpy_word(seg, seed):
-    # counter ((uint64) seg, 0, 0, 0); NumPy advances it before its block
-    v = ((seg % 2 ** 64) - 1) % 2 ** 256
+    # counter (seg mod 256, 0, 0, 0); NumPy advances it before its block
+    v = ((seg % 256) - 1) % 2 ** 256
     c = np.array([(v >> (64 * j)) & (2 ** 64 - 1) for j in range(4)], dtype=np.uint64)
     k = np.array([seed, MIG_KEY1], dtype=np.uint64)
     return int(np.random.Philox(counter=c, key=k).random_raw(1)[0])
@@ -94,6 +95,8 @@ def test_segment_maps_follow_the_generator(orc):
     for seg in list(range(-5, 60)) + [10 ** 6, -(10 ** 6)]:
         k = orc.migration_info(m, 0, seg)["map_of_segment"]
         assert k == numpy_word(seg, 1234) % 3
+        # the choice repeats every 256 segments
+        assert k == orc.migration_info(m, 0, seg + 256 * 7)["map_of_segment"]
         seen.add(k)
     assert seen == {0, 1, 2}
 

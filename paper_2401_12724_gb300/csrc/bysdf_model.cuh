@@ -390,18 +390,22 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   // centre's radial direction; fiber phase in map periods; 1D map lookup
   const S u_ply = xatan2(best_c * np.y - best_s * np.x, best_c * np.x + best_s * np.y);
   const S w = u_ply * m.m_over_2pi - phase_f_v - mv.kf * dz;
-  // map 0's phase, or the migration maps' (Sec. 3.5)
-  const float2* mp = map;
-  const float2* mp1 = map;
-  S wv = w, wv1 = w, wgt = S(0.f);
-  if (m.mig_maps > 1) migration_maps(m, map, mv, u_ply, v, dz, w, &mp, &wv, &mp1, &wv1, &wgt);
+  // map 0, or the migration maps of the hit's segment (Sec. 3.5)
   S delta, of;
-  fiber_lookup(mp, m.T, wv, &delta, &of);
-  if (vf(wgt) > 0.f) {
-    S d1, o1;
-    fiber_lookup(mp1, m.T, wv1, &d1, &o1);
-    delta = delta + wgt * (d1 - delta);
-    of = of + wgt * (o1 - of);
+  if (m.mig_maps > 1) {
+    const float2* mp = map;
+    const float2* mp1 = map;
+    S wv = w, wv1 = w, wgt = S(0.f);
+    migration_maps(m, map, mv, u_ply, v, dz, w, &mp, &wv, &mp1, &wv1, &wgt);
+    fiber_lookup(mp, m.T, wv, &delta, &of);
+    if (vf(wgt) > 0.f) {
+      S d1, o1;
+      fiber_lookup(mp1, m.T, wv1, &d1, &o1);
+      delta = delta + wgt * (d1 - delta);
+      of = of + wgt * (o1 - of);
+    }
+  } else {
+    fiber_lookup(map, m.T, w, &delta, &of);
   }
   // n_f = n'(R(n_p)), t_f = t'(R(t_p))
   out.tf = tp * mv.cos_af + ep * mv.sin_af;

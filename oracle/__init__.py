@@ -38,6 +38,7 @@ from .oracle import (  # noqa: F401
     sample_records,
     sample_stochastic_records,
     stoch_nodes,
+    trace_yarns,
     vndf_pdf,
     vndf_sample,
 )

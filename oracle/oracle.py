@@ -11,6 +11,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bysdf_oracle.cpp")
 _HDR = os.path.join(_HERE, "bysdf_oracle.h")
+_SRC_TRACE = os.path.join(_HERE, "yarn_trace.cpp")
+_HDR_TRACE = os.path.join(_HERE, "yarn_trace.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 NPARAM = 8
 NPARAM_EXT = 15   # NPARAM, then r, k^B_y (RGB), sigma_t, B, k_spec
@@ -44,6 +46,16 @@ class Material(C.Structure):
         ("migration_length", C.c_double),
         ("migration_blend", C.c_double),
     ]
+
+
+class Yarn(C.Structure):
+    _fields_ = [("p0", C.c_double * 3), ("t", C.c_double * 3), ("n_ref", C.c_double * 3),
+                ("length", C.c_double), ("radius", C.c_double), ("v0", C.c_double),
+                ("mat_id", C.c_int32), ("pad", C.c_int32)]
+
+
+class RayPlanes(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("o", "d", "o1", "d1", "o2", "d2")]
 
 
 class Records(C.Structure):
@@ -89,12 +101,13 @@ def build(force: bool = False) -> str:
     """Compile the oracle with g++ (IEEE double, no FMA contraction)."""
     with _lock:
         stale = (not os.path.exists(_LIB)) or any(
-            os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+            os.path.getmtime(p) > os.path.getmtime(_LIB)
+            for p in (_SRC, _HDR, _SRC_TRACE, _HDR_TRACE))
         if force or stale:
             tmp = _LIB + f".tmp{os.getpid()}"
             subprocess.check_call([
                 "g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC",
-                "-shared", "-o", tmp, _SRC, "-lpthread"])
+                "-shared", "-o", tmp, _SRC, _SRC_TRACE, "-lpthread"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -119,6 +132,8 @@ def lib():
         L.orc_stoch_nodes.argtypes = [C.c_double, C.c_int, C.c_double, C.c_int, C.c_uint64,
                                       C.c_uint64, P]
         L.orc_philox4x64.argtypes = [P, P, P]
+        L.orc_trace_yarns.argtypes = [P, C.c_int, C.POINTER(RayPlanes), C.c_int64, P, P, P, P,
+                                      P, P, P, P, P, P, C.c_int]
         L.orc_migration_info.argtypes = [MP, C.c_int, C.c_int64, P]
         L.orc_migration_texels.argtypes = [MP, C.c_int, P, P]
         L.orc_philox4x64.restype = None
@@ -329,6 +344,37 @@ def migration_texels(mat, k: int):
     if lib().orc_migration_texels(C.byref(_material(mat)), k, dl.ctypes.data, of.ctypes.data):
         raise ValueError("oracle: bad material description or map index")
     return dl, of
+
+
+def trace_yarns(yarns, rays: dict, light, threads: int = 1) -> dict:
+    """Camera rays against yarn pieces (yarn_trace.h).  yarns: list of dicts
+    (p0, t, n_ref, length, radius, v0, mat_id); rays: float32 [3, n] planes
+    o, d and optionally o1, d1, o2, d2."""
+    arr = (Yarn * len(yarns))()
+    for k, yd in enumerate(yarns):
+        for f in ("p0", "t", "n_ref"):
+            for c in range(3):
+                getattr(arr[k], f)[c] = float(np.float32(yd[f][c]))
+        arr[k].length = float(np.float32(yd["length"]))
+        arr[k].radius = float(np.float32(yd["radius"]))
+        arr[k].v0 = float(np.float32(yd["v0"]))
+        arr[k].mat_id = int(yd["mat_id"])
+    keep = []
+    rp = RayPlanes()
+    n = int(np.asarray(rays["o"]).shape[1])
+    for k in ("o", "d", "o1", "d1", "o2", "d2"):
+        if rays.get(k) is not None:
+            a = np.ascontiguousarray(rays[k], dtype=np.float32).reshape(3, n)
+            keep.append(a)
+            setattr(rp, k, a.ctypes.data)
+    out = {k: np.zeros(n) for k in ("h", "u", "v", "ratio", "t_hit")}
+    out["wi"] = np.zeros((3, n)); out["wo"] = np.zeros((3, n))
+    out["yarn"] = np.zeros(n, np.int32); out["mat_id"] = np.zeros(n, np.int32)
+    lt = np.ascontiguousarray(light, dtype=np.float64)
+    lib().orc_trace_yarns(arr, len(yarns), C.byref(rp), n, lt.ctypes.data,
+                          *(out[k].ctypes.data for k in ("h", "u", "v", "wi", "wo", "ratio",
+                                                         "t_hit", "yarn", "mat_id")), threads)
+    return out
 
 
 def philox4x64(ctr, key):

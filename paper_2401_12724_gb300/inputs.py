@@ -231,3 +231,92 @@ def random_records(n: int, n_mat: int = 1, seed: int = 1, wi_mode: str = "sphere
 def seg_offsets_from_ids(mat_id: np.ndarray, n_mat: int) -> np.ndarray:
     c = np.bincount(np.asarray(mat_id), minlength=n_mat)
     return np.concatenate([[0], np.cumsum(c)]).astype(np.int64)
+
+
+# ----------------------------------------------------------------- scenes --
+def _rmf_normals(points: np.ndarray, n0: np.ndarray) -> np.ndarray:
+    """Reference normals of the pieces of a polyline, carried from n0 by the
+    double-reflection rule for rotation-minimising frames (Wang, Juettler,
+    Zheng, Liu 2008): reflect across the plane bisecting consecutive piece
+    starts, then across the plane bisecting the two tangents."""
+    t = np.diff(points, axis=0)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    out = np.zeros_like(t)
+    r = n0 - t[0] * (n0 @ t[0])
+    out[0] = r / np.linalg.norm(r)
+    for k in range(len(t) - 1):
+        v1 = points[k + 1] - points[k]
+        c1 = v1 @ v1
+        rl = out[k] - (2.0 / c1) * (v1 @ out[k]) * v1
+        tl = t[k] - (2.0 / c1) * (v1 @ t[k]) * v1
+        v2 = t[k + 1] - tl
+        c2 = v2 @ v2
+        rn = rl - (2.0 / c2) * (v2 @ rl) * v2 if c2 > 1e-30 else rl
+        rn -= t[k + 1] * (rn @ t[k + 1])
+        out[k + 1] = rn / np.linalg.norm(rn)
+    return out
+
+
+def woven_scene(n_yarns: int = 16, pieces: int = 16, radius: float = 1.0,
+                spacing: float = 2.5, lift: float = 0.6, n_mat: int = 8,
+                seed: int = 0) -> list[dict]:
+    """A plain-weave patch: n_yarns warp yarns along x and n_yarns weft yarns
+    along y, each a polyline of straight pieces alternating over (+lift) and
+    under (-lift) at the crossings; materials drawn per yarn.  Returns the
+    pieces as dicts (p0, t, n_ref, length, radius, v0, mat_id)."""
+    g = np.random.Generator(np.random.Philox(key=[SEED_BASE + 500, seed]))
+    ids = g.integers(0, n_mat, 2 * n_yarns)
+    out = []
+    span = np.arange(pieces + 1) * spacing
+    for axis in (0, 1):
+        for j in range(n_yarns):
+            z = np.where((np.arange(pieces + 1) + j + axis) % 2 == 0, lift, -lift)
+            pts = np.zeros((pieces + 1, 3))
+            pts[:, axis] = span
+            pts[:, 1 - axis] = (j + 0.5) * spacing
+            pts[:, 2] = z
+            nref = _rmf_normals(pts, np.array([0.0, 0.0, 1.0]))
+            v0 = 0.0
+            for k in range(pieces):
+                d = pts[k + 1] - pts[k]
+                L = float(np.linalg.norm(d))
+                out.append(dict(p0=pts[k].tolist(), t=(d / L).tolist(), n_ref=nref[k].tolist(),
+                                length=L, radius=radius, v0=v0,
+                                mat_id=int(ids[axis * n_yarns + j])))
+                v0 += L
+    return out
+
+
+def camera_rays(width: int, height: int, extent: float, elevation_deg: float = 55.0,
+                distance: float | None = None, fov_deg: float = 30.0,
+                jitter_seed: int | None = None) -> dict:
+    """Pinhole camera over a square patch [0, extent]^2 at z = 0, looking at
+    its centre from the given elevation (by default from the distance at
+    which the patch's inner 80% fills the image width); rays o, d as float32
+    [3, n] planes (row-major pixels) and two differential rays through the
+    pixel's opposite corners (o1, d1, o2, d2)."""
+    c = np.array([extent / 2, extent / 2, 0.0])
+    if distance is None:
+        distance = 0.4 * extent / math.tan(math.radians(fov_deg) / 2)
+    el = math.radians(elevation_deg)
+    eye = c + distance * np.array([0.0, -math.cos(el), math.sin(el)])
+    fwd = (c - eye) / np.linalg.norm(c - eye)
+    right = np.cross(fwd, [0.0, 0.0, 1.0])
+    right /= np.linalg.norm(right)
+    up = np.cross(right, fwd)
+    tan_h = math.tan(math.radians(fov_deg) / 2)
+    ys, xs = np.mgrid[0:height, 0:width]
+    px, py = xs.ravel().astype(np.float64), ys.ravel().astype(np.float64)
+    if jitter_seed is not None:
+        g = np.random.Generator(np.random.Philox(key=[SEED_BASE + 501, jitter_seed]))
+        px = px + g.random(px.size) - 0.5
+        py = py + g.random(py.size) - 0.5
+
+    def dirs(ox, oy):
+        sx = ((px + 0.5 + ox) / width * 2 - 1) * tan_h
+        sy = (1 - (py + 0.5 + oy) / height * 2) * tan_h * height / width
+        d = fwd[:, None] + right[:, None] * sx + up[:, None] * sy
+        return (d / np.linalg.norm(d, axis=0)).astype(np.float32)
+    n = px.size
+    o = np.repeat(eye[:, None], n, axis=1).astype(np.float32)
+    return dict(o=o, d=dirs(0.0, 0.0), o1=o, d1=dirs(0.5, 0.5), o2=o, d2=dirs(-0.5, -0.5))

@@ -494,6 +494,32 @@ def other_workloads(api, N, torch, args, sm_count):
                                                         records=n)
     del d, o
     torch.cuda.empty_cache()
+    # upstream step: 2048 x 2048 camera rays against a plain-weave patch of
+    # 32 yarns cut into 512 straight pieces, then the fused BYSDF on the
+    # traced records (8 materials)
+    sc = I.woven_scene(16, 16)
+    Y = api.yarns_to_device(sc)
+    rays = {k: torch.from_numpy(v).cuda() for k, v in
+            I.camera_rays(2048, 2048, extent=16 * 2.5).items()}
+    n = int(rays["o"].shape[1])
+    light = (0.3, -0.4, math.sqrt(0.75))
+    tr = api.trace_yarns(Y, rays, light)
+    rec_t = dict(h=tr["h"], u=tr["u"], v=tr["v"], wi=tr["wi"], wo=tr["wo"], ratio=tr["ratio"],
+                 mat_id=tr["mat_id"], u0=torch.rand(n, device="cuda") * 0.9999,
+                 u1=torch.rand(n, device="cuda") * 0.9999)
+    M = api.Materials(I.materials(2))
+    o = api.alloc_fused(n, "cuda")
+    ms_tr, _ = timed(lambda: api.trace_yarns(Y, rays, light, out=tr), max(3, steps // 4), 2)
+
+    def render_step():
+        api.trace_yarns(Y, rays, light, out=tr)
+        api.eval_sample_pdf(M, rec_t, out=o)
+    ms_rs, _ = timed(render_step, max(3, steps // 4), 2)
+    res["trace-512pieces-2048x2048+fused"] = dict(
+        rays_per_s=n / (ms_rs / 1e3), ms=ms_rs, rays=n, trace_only_rays_per_s=n / (ms_tr / 1e3),
+        trace_ms=ms_tr, hit_share=float((tr["mat_id"] >= 0).float().mean()))
+    del rays, tr, rec_t, o
+    torch.cuda.empty_cache()
     # batched heterogeneous: 256 materials, Zipf counts, one persistent
     # material-sorted launch per op captured in a CUDA graph, vs plain
     mats = I.materials(4)

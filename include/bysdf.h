@@ -259,6 +259,57 @@ int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits*
                                      float* pdf_s, uint8_t* lobe_status_s, void* workspace,
                                      size_t workspace_bytes, void* stream);
 
+/* ---- The step upstream of the BYSDF: rays against explicit yarns ----
+ * Yarns (Sec. 3.3) are curves cut into straight pieces; a straight piece's
+ * rotation-minimising frame is constant, so each piece carries its reference
+ * normal.  bysdf_trace_yarns finds, per camera ray, the closest entry into
+ * the lateral surface of any piece (end caps are not surfaces; a ray
+ * starting inside a piece sees none of that piece) and writes the BYSDF hit
+ * record in the piece's frame (x = reference normal, y = tangent x normal,
+ * z = tangent):
+ *   u  azimuth of the surface normal at the hit, [0, 2 pi);
+ *   h  the azimuthal offset: the ray's signed distance from the axis in the
+ *      cross-section over R, in [-1, 1];
+ *   v  v0 + position along the piece;
+ *   wi = -d, wo = the light direction, in the frame (3 planes each);
+ *   ratio (optional): with the two differential rays (Sec. 5.3), the larger
+ *      |h_k - h| of their own azimuthal offsets about the same axis (hit or
+ *      not), i.e. the pixel footprint's half-width in h (2 for a ray along
+ *      the axis); without them 0 (near field);
+ *   mat_id: the piece's material; -1 where no piece is hit (the other
+ *      outputs are then 0; the BYSDF reports such records as invalid).
+ * Each piece's frame is made orthonormal (t / |t|, then n_ref without its t
+ * component, normalised).  Every ray tests every piece (staged in shared
+ * memory): the cost grows with the piece count; at most 2048 pieces. */
+typedef struct bysdf_yarn {
+  float p0[3];       /* root of the piece */
+  float tangent[3];  /* along the piece (unit) */
+  float n_ref[3];    /* reference normal, perpendicular to the tangent */
+  float length;      /* of the piece */
+  float radius;      /* R */
+  float v0;          /* length along the yarn at the root */
+  int32_t mat_id;    /* material of the piece */
+  int32_t pad[3];
+} bysdf_yarn;
+
+typedef struct bysdf_rays {
+  const float* o;    /* ray origins, 3 planes */
+  const float* d;    /* ray directions (unit), 3 planes */
+  const float* o1;   /* differential rays: NULL for none */
+  const float* d1;
+  const float* o2;
+  const float* d2;
+} bysdf_rays;
+
+/* yarns: DEVICE array of n_yarns pieces (1..2048); rays and outputs: DEVICE
+ * planes of n rays (16-byte aligned); light: HOST, 3 floats (unit, world).
+ * ratio, yarn_id (piece index or -1) and t_hit (ray parameter) may be NULL.
+ * Stream-ordered; returns BYSDF_E_ARG on bad sizes or pointers. */
+int bysdf_trace_yarns(const bysdf_yarn* yarns, int32_t n_yarns, const bysdf_rays* rays,
+                      int64_t n, const float light[3], float* h, float* u, float* v,
+                      float* wi, float* wo, float* ratio, int32_t* mat_id, int32_t* yarn_id,
+                      float* t_hit, void* stream);
+
 /* Gradient of sum_i sum_c grad_f[c][i] * f_c(record i) with respect to the 8
  * parameters of each material (layout of bysdf_set_params), accumulated
  * into grad_params[n_mat][8] (DEVICE, zeroed by this call).  The forward pass

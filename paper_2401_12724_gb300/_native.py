@@ -49,6 +49,10 @@ class Stochastic(C.Structure):
 
 STOCH_JITTER_NODES, STOCH_ROUGH_ENTRY = 1, 2
 
+
+class Rays(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("o", "d", "o1", "d1", "o2", "d2")]
+
 # (name, restype, argtypes) of every symbol declared in include/bysdf.h
 P = C.c_void_p
 SYMBOLS = [
@@ -72,6 +76,9 @@ SYMBOLS = [
     ("bysdf_eval_sample_pdf_stochastic", C.c_int,
      [P, C.POINTER(Hits), C.POINTER(Stochastic), P, P, C.c_int64, P, P, P, P, P, P, P, P,
       C.c_size_t, P]),
+    ("bysdf_trace_yarns", C.c_int,
+     [P, C.c_int32, C.POINTER(Rays), C.c_int64, C.POINTER(C.c_float), P, P, P, P, P, P, P, P, P,
+      P]),
     ("bysdf_eval_backward", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_eval_backward_ext", C.c_int,
      [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_int, P, C.c_size_t, P]),

@@ -262,6 +262,45 @@ def eval_sample_pdf_stochastic(mats: Materials, rec: dict, seed: int, flags: int
     return o
 
 
+def yarns_to_device(pieces, device="cuda") -> torch.Tensor:
+    """Yarn pieces (dicts: p0, t, n_ref, length, radius, v0, mat_id) packed as
+    the bysdf_yarn struct (64 bytes each) in device memory."""
+    n = len(pieces)
+    f = np.zeros((n, 16), np.float32)
+    for k, y in enumerate(pieces):
+        f[k, 0:3] = y["p0"]
+        f[k, 3:6] = y["t"]
+        f[k, 6:9] = y["n_ref"]
+        f[k, 9:12] = (y["length"], y["radius"], y["v0"])
+    words = f.view(np.int32)
+    words[:, 12] = [int(y["mat_id"]) for y in pieces]
+    words[:, 13:16] = 0
+    return torch.from_numpy(words.copy()).to(device)
+
+
+def trace_yarns(yarns: torch.Tensor, rays: dict, light, stream=None, out=None) -> dict:
+    """Camera rays (device planes o, d and optionally o1, d1, o2, d2) against
+    the packed yarn pieces: the BYSDF hit records (h, u, v, wi, wo, ratio,
+    mat_id) plus yarn_id and t_hit."""
+    n = int(rays["o"].shape[-1])
+    dev = rays["o"].device
+    o = out if out is not None else dict(
+        h=_empty((n,), torch.float32, dev), u=_empty((n,), torch.float32, dev),
+        v=_empty((n,), torch.float32, dev), wi=_empty((3, n), torch.float32, dev),
+        wo=_empty((3, n), torch.float32, dev), ratio=_empty((n,), torch.float32, dev),
+        mat_id=_empty((n,), torch.int32, dev), yarn_id=_empty((n,), torch.int32, dev),
+        t_hit=_empty((n,), torch.float32, dev))
+    r = N.Rays(*[_ptr(rays.get(k)) for k in ("o", "d", "o1", "d1", "o2", "d2")])
+    lt = (C.c_float * 3)(*[float(x) for x in light])
+    lib = N.load()
+    N.check(lib.bysdf_trace_yarns(_ptr(yarns), int(yarns.shape[0]), C.byref(r), n, lt,
+                                  _ptr(o["h"]), _ptr(o["u"]), _ptr(o["v"]), _ptr(o["wi"]),
+                                  _ptr(o["wo"]), _ptr(o.get("ratio")), _ptr(o["mat_id"]),
+                                  _ptr(o.get("yarn_id")), _ptr(o.get("t_hit")), _stream(stream)),
+            "bysdf_trace_yarns")
+    return o
+
+
 def eval_backward(mats: Materials, rec: dict, grad_f: torch.Tensor, deterministic: bool = False,
                   stream=None, out=None) -> torch.Tensor:
     """d(sum grad_f * f) / d params, shape (n_mat, 8)."""

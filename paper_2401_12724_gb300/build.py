@@ -14,7 +14,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libbysdf.so")
 SOURCES = ["bysdf_api.cu", "bysdf_fwd.cu", "bysdf_fwd_eval.cu", "bysdf_fwd_sample.cu",
-           "bysdf_fwd_pdf.cu", "bysdf_fwd_fused.cu", "bysdf_fwd_stoch.cu", "bysdf_bwd.cu"]
+           "bysdf_fwd_pdf.cu", "bysdf_fwd_fused.cu", "bysdf_fwd_stoch.cu", "bysdf_bwd.cu",
+           "bysdf_trace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -1015,6 +1015,55 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
                      reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED]);
 }
 
+int bysdf_trace_yarns(const bysdf_yarn* yarns, int32_t n_yarns, const bysdf_rays* rays,
+                      int64_t n, const float light[3], float* h, float* u, float* v,
+                      float* wi, float* wo, float* ratio, int32_t* mat_id, int32_t* yarn_id,
+                      float* t_hit, void* stream) {
+  if (!yarns || !rays || !light) return fail(BYSDF_E_ARG, "yarns, rays and light are required");
+  if (n_yarns < 1 || n_yarns > kMaxYarnPieces) return fail(BYSDF_E_ARG, "n_yarns outside [1, 2048]");
+  if (n < 0 || n > ((int64_t)1 << 36)) return fail(BYSDF_E_ARG, "n out of range");
+  if (n == 0) return BYSDF_OK;
+  if (!rays->o || !rays->d) return fail(BYSDF_E_ARG, "rays: o and d required");
+  const bool diff = rays->o1 || rays->d1 || rays->o2 || rays->d2;
+  if (diff && !(rays->o1 && rays->d1 && rays->o2 && rays->d2))
+    return fail(BYSDF_E_ARG, "rays: give all four differential planes or none");
+  const void* ins[] = {rays->o, rays->d, rays->o1, rays->d1, rays->o2, rays->d2};
+  for (const void* p : ins)
+    if (p && !aligned16(p)) return fail(BYSDF_E_ARG, "rays: buffer not 16-byte aligned");
+  int rc;
+  if ((rc = check_out(h, "h")) || (rc = check_out(u, "u")) || (rc = check_out(v, "v")) ||
+      (rc = check_out(wi, "wi")) || (rc = check_out(wo, "wo")) || (rc = check_out(mat_id, "mat_id")))
+    return rc;
+  if (ratio && !aligned16(ratio)) return fail(BYSDF_E_ARG, "ratio not 16-byte aligned");
+  const float ln = std::sqrt(light[0] * light[0] + light[1] * light[1] + light[2] * light[2]);
+  if (!(std::fabs(ln - 1.0f) <= 1e-3f)) return fail(BYSDF_E_ARG, "light must be a unit vector");
+  TraceArgs a{};
+  a.o = rays->o;
+  a.d = rays->d;
+  a.o1 = rays->o1;
+  a.d1 = rays->d1;
+  a.o2 = rays->o2;
+  a.d2 = rays->d2;
+  a.n = n;
+  for (int c = 0; c < 3; ++c) a.light[c] = light[c];
+  a.h = h;
+  a.u = u;
+  a.v = v;
+  a.wi = wi;
+  a.wo = wo;
+  a.ratio = ratio;
+  a.t_hit = t_hit;
+  a.mat_id = mat_id;
+  a.yarn_id = yarn_id;
+  int dev = 0, sms = 0;
+  BY_CU(cudaGetDevice(&dev));
+  BY_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t blocks = (n + 255) / 256;
+  const int grid = (int)std::min<int64_t>(blocks, (int64_t)sms * 8);
+  BY_CU(launch_trace_yarns(yarns, n_yarns, a, grid, reinterpret_cast<cudaStream_t>(stream)));
+  return BYSDF_OK;
+}
+
 int bysdf_eval_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
                           const bysdf_stochastic* sto, int64_t n, float* f_rgb, float* pdf,
                           uint8_t* status, void* workspace, size_t workspace_bytes,

@@ -3,9 +3,22 @@
 
 #include <cuda_runtime.h>
 
+#include "bysdf.h"
 #include "bysdf_kernels.cuh"
 
 namespace bysdf {
+
+// camera rays -> hit records (bysdf_trace_yarns)
+struct TraceArgs {
+  const float *o, *d, *o1, *d1, *o2, *d2;
+  int64_t n;
+  float light[3];
+  float *h, *u, *v, *wi, *wo, *ratio, *t_hit;
+  int32_t *mat_id, *yarn_id;
+};
+constexpr int kMaxYarnPieces = 2048;  // 64 bytes each in shared memory
+cudaError_t launch_trace_yarns(const bysdf_yarn* yarns, int n_yarns, const TraceArgs& a,
+                               int grid, cudaStream_t st);
 
 // op: OPF_* bit set (EVAL, SAMPLE, PDF, EVAL|SAMPLE).  Returns the launch error.
 cudaError_t launch_forward(int op, const KArgs& a, int block, int occ, int grid, size_t smem,

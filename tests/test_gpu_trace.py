@@ -1,0 +1,105 @@
+"""GPU parity of the ray-yarn step (bysdf_trace_yarns) against the oracle, and
+the traced records fed end to end into the BYSDF kernels."""
+import math
+
+import numpy as np
+import pytest
+
+import parity_util as PU
+from paper_2401_12724_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+LIGHT = (0.3, -0.4, math.sqrt(0.75))
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_12724_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def traced(api, orc, n_yarns=6, pieces=6, w=96, h=80):
+    sc = I.woven_scene(n_yarns, pieces)
+    rays = I.camera_rays(w, h, extent=pieces * 2.5, jitter_seed=5)
+    Y = api.yarns_to_device(sc)
+    rd = {k: torch.from_numpy(v).cuda() for k, v in rays.items()}
+    g = {k: np_(v) for k, v in api.trace_yarns(Y, rd, LIGHT).items()}
+    o = orc.trace_yarns(sc, rays, np.array(LIGHT), threads=8)
+    return sc, rays, g, o
+
+
+def test_trace_matches_oracle(api, orc):
+    sc, rays, g, o = traced(api, orc)
+    PU.dump("trace", **{"g_" + k: v for k, v in g.items()}, **{"o_" + k: v for k, v in o.items()})
+    same = g["yarn_id"] == o["yarn"]
+    # ties between pieces meeting at a joint, and grazing rays, may go either
+    # way in float32
+    assert same.mean() >= 0.995, same.mean()
+    hit = same & (o["yarn"] >= 0)
+    assert hit.mean() > 0.8
+    assert np.all(g["mat_id"][hit] == o["mat_id"][hit])
+    du = np.abs(np.angle(np.exp(1j * (g["u"][hit] - o["u"][hit]))))
+    assert np.quantile(du, 0.999) < 2e-5 and du.max() < 1e-3, du.max()
+    dh = np.abs(g["h"][hit] - o["h"][hit])
+    assert np.quantile(dh, 0.999) < 2e-5 and dh.max() < 1e-3, dh.max()
+    np.testing.assert_allclose(g["v"][hit], o["v"][hit], rtol=1e-6, atol=2e-5)
+    np.testing.assert_allclose(g["wi"][:, hit], o["wi"][:, hit], atol=2e-6)
+    np.testing.assert_allclose(g["wo"][:, hit], o["wo"][:, hit], atol=2e-6)
+    np.testing.assert_allclose(g["t_hit"][hit], o["t_hit"][hit], rtol=1e-5)
+    dr = np.abs(g["ratio"][hit] - o["ratio"][hit])
+    assert np.quantile(dr, 0.999) < 1e-4 + 1e-3 * np.quantile(o["ratio"][hit], 0.999)
+    miss = same & (o["yarn"] < 0)
+    assert np.all(g["mat_id"][miss] == -1)
+
+
+def test_traced_records_feed_the_bysdf(api, orc):
+    # GPU trace -> GPU fused eval + sample, against the oracle BYSDF on the
+    # same (GPU-traced) records
+    sc, rays, g, _ = traced(api, orc, w=128, h=96)
+    mats = I.materials(2)
+    n = g["h"].size
+    rng = np.random.default_rng(7)
+    rec = dict(h=g["h"], u=g["u"], v=g["v"], wi=g["wi"], wo=g["wo"], ratio=g["ratio"],
+               mat_id=g["mat_id"],
+               u0=np.minimum(rng.random(n), 1 - 2 ** -24).astype(np.float32),
+               u1=np.minimum(rng.random(n), 1 - 2 ** -24).astype(np.float32))
+    M = api.Materials(mats)
+    d = api.records_to_device(rec, "cuda")
+    out = api.eval_sample_pdf(M, d)
+    f, p, st = np_(out["f"]), np_(out["pdf"]), np_(out["status"])
+    assert np.all(st[g["mat_id"] < 0] == 2)
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, rec)
+    PU.assert_status(st, sb, [q[2] for q in pert], "trace.status")
+    PU.assert_parity(f, fb, [q[0] for q in pert], "trace.f")
+    PU.assert_parity(p, pb, [q[1] for q in pert], "trace.pdf")
+    assert (st == 0).mean() > 0.5
+
+
+def test_trace_argument_errors(api):
+    sc = I.woven_scene(2, 2)
+    Y = api.yarns_to_device(sc)
+    rays = {k: torch.from_numpy(v).cuda() for k, v in I.camera_rays(8, 8, 5.0).items()}
+    with pytest.raises(RuntimeError, match="unit"):
+        api.trace_yarns(Y, rays, (1.0, 1.0, 0.0))
+    with pytest.raises(RuntimeError, match="yarns"):
+        api.trace_yarns(Y[:0], rays, LIGHT)
+    partial = dict(rays)
+    partial.pop("d2")
+    with pytest.raises(RuntimeError, match="differential"):
+        api.trace_yarns(Y, partial, LIGHT)

@@ -53,7 +53,7 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="5a9f42b16d38e92072699d6739475b444b2c37764ef18b47a1bda9db005657ad",
+TRAFFIC_CAPTURE = dict(sources_sha256="bb93f164d5949d173659fd79e65112b7ff72a4cdd5f763eba2965adf89aa0275",
                        bytes_per_record=85.10,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
@@ -279,9 +279,10 @@ def main():
                     help="main workload only, no clocks/e2e/CPU baseline (for ncu)")
     ap.add_argument("--records", type=int, default=0,
                     help="use only the first N records of the workload (profiling)")
-    ap.add_argument("--profile-op", default="fused", choices=["fused", "backward"],
+    ap.add_argument("--profile-op", default="fused", choices=["fused", "backward", "trace"],
                     help="with --profile: fused = eval + sample + pdf over workload 2; "
-                         "backward = forward eval + backward over workload 5")
+                         "backward = forward eval + backward over workload 5; trace = "
+                         "2048 x 2048 camera rays against a 512-piece yarn patch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -301,6 +302,17 @@ def main():
 
     if args.profile and args.profile_op == "backward":
         profile_backward(api, torch, args, rank)
+        return
+    if args.profile and args.profile_op == "trace":
+        sc = I.woven_scene(16, 16)
+        Y = api.yarns_to_device(sc)
+        rays = {k: torch.from_numpy(v).cuda() for k, v in
+                I.camera_rays(2048, 2048, extent=16 * 2.5).items()}
+        light = (0.3, -0.4, math.sqrt(0.75))
+        tr = api.trace_yarns(Y, rays, light)
+        ms, _ = timed(lambda: api.trace_yarns(Y, rays, light, out=tr), args.steps, args.warmup)
+        print(json.dumps(dict(profile="trace", rays=int(rays["o"].shape[1]), ms_per_step=ms)),
+              flush=True)
         return
 
     # ---------------------------------------------- main workload (fused) --

@@ -279,8 +279,14 @@ int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits*
  *   mat_id: the piece's material; -1 where no piece is hit (the other
  *      outputs are then 0; the BYSDF reports such records as invalid).
  * Each piece's frame is made orthonormal (t / |t|, then n_ref without its t
- * component, normalised).  Every ray tests every piece (staged in shared
- * memory): the cost grows with the piece count; at most 2048 pieces. */
+ * component, normalised).  The pieces are staged in shared memory (at most
+ * 2048) and grouped in eights in the order given, each group and each piece
+ * with a bounding sphere: giving the pieces of a yarn consecutively keeps the
+ * groups tight.  A warp of 32 consecutive rays skips the groups and pieces
+ * that no ray of it can reach, so the cost follows the pieces near the rays
+ * when neighbouring rays are coherent (camera rays in pixel order); the
+ * result is that of testing every piece.  A ray with a zero or non-finite
+ * direction, or a non-finite origin, hits nothing (mat_id -1). */
 typedef struct bysdf_yarn {
   float p0[3];       /* root of the piece */
   float tangent[3];  /* along the piece (unit) */

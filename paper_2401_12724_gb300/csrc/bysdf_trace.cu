@@ -3,11 +3,18 @@
 //
 // Yarns are straight pieces of yarn curves staged in shared memory (a
 // piece's rotation-minimising frame is constant, so it carries its reference
-// normal).  One thread per ray tests every piece: a conservative bounding-
-// sphere distance test first, then the lateral surface about the ray's point
-// of closest approach to the axis, where the square root is taken of R^2
-// minus a small distance (no cancellation between terms of the camera
-// distance squared).
+// normal).  One thread per ray; pieces carry a bounding sphere, and so do
+// groups of kGroupPieces consecutive pieces (neighbours along a yarn, in the
+// caller's order).  The rays of a warp are neighbouring pixels, so the warp
+// culls against a bound on all 32 rays at once: it tests 32 groups at a time,
+// one per lane, then the pieces of up to four kept groups at a time, one per
+// lane, and keeps the ballot of the pieces some ray may reach.  Each ray then
+// tests the kept pieces in ascending order: a conservative bounding-sphere
+// distance test, then the lateral surface about the ray's point of closest
+// approach to the axis, where the square root is taken of R^2 minus a small
+// distance (no cancellation between terms of the camera distance squared).
+// The culling only skips pieces that no ray of the warp can hit: the result
+// is that of testing every piece.
 #include "bysdf_launch.h"
 
 namespace bysdf {
@@ -39,12 +46,32 @@ __device__ __forceinline__ float line_offset(const PieceS& p, float bx, float by
   return (q_n * d_b - q_b * d_n) / (l * p.b.w);
 }
 
+constexpr int kGroupPieces = 8;
+
+// The line of a ray with origin o_i and unit direction u_i lies at least
+// dist(C, axis) - ro - (|C - oc| + ro) * del from a point C, where the axis
+// is (oc, ua), ro >= |o_i - oc| and del >= |u_i - ua|: a sphere (C, r^2)
+// farther than r plus that slack from the axis is missed by every ray of the
+// bundle.  A bound that is not finite (a degenerate ray) keeps the sphere.
+__device__ __forceinline__ bool bundle_reaches(float4 sph, float ocx, float ocy, float ocz,
+                                               float uax, float uay, float uaz, float ro,
+                                               float del) {
+  const float vx = sph.x - ocx, vy = sph.y - ocy, vz = sph.z - ocz;
+  const float tv = dot3(vx, vy, vz, uax, uay, uaz);
+  const float px = fmaf(-tv, uax, vx), py = fmaf(-tv, uay, vy), pz = fmaf(-tv, uaz, vz);
+  const float thr =
+      fmaf(sqrtf(dot3(vx, vy, vz, vx, vy, vz)) + ro, del, sqrtf(sph.w) + ro) * 1.0001f + 1e-4f;
+  return !(dot3(px, py, pz, px, py, pz) > thr * thr);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restrict__ yarns,
                                                      int n_yarns, TraceArgs a) {
   extern __shared__ float4 smem_pieces[];
   PieceS* ps = reinterpret_cast<PieceS*>(smem_pieces);
+  const int n_grp = (n_yarns + kGroupPieces - 1) / kGroupPieces;
+  float4* grp = smem_pieces + 4 * n_yarns;  // (centre, squared radius) per group
   // stage the pieces with an orthonormal frame: t / |t|, then n_ref without
   // its t component, normalised; bounding sphere about the piece's centre
   for (int k = threadIdx.x; k < n_yarns; k += blockDim.x) {
@@ -73,43 +100,120 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
     ps[k] = p;
   }
   __syncthreads();
+  // group spheres: the box around the pieces' spheres, then the largest
+  // reach from its centre, widened like the piece spheres
+  for (int c = threadIdx.x; c < n_grp; c += blockDim.x) {
+    const int k0 = c * kGroupPieces, k1 = min(k0 + kGroupPieces, n_yarns);
+    float lx = 3.4e38f, ly = 3.4e38f, lz = 3.4e38f, hx = -3.4e38f, hy = -3.4e38f, hz = -3.4e38f;
+    for (int k = k0; k < k1; ++k) {
+      const float4 d = ps[k].d;
+      const float r = sqrtf(d.w);
+      lx = fminf(lx, d.x - r);
+      ly = fminf(ly, d.y - r);
+      lz = fminf(lz, d.z - r);
+      hx = fmaxf(hx, d.x + r);
+      hy = fmaxf(hy, d.y + r);
+      hz = fmaxf(hz, d.z + r);
+    }
+    const float cx = 0.5f * (lx + hx), cy = 0.5f * (ly + hy), cz = 0.5f * (lz + hz);
+    float R = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const float4 d = ps[k].d;
+      const float ex = d.x - cx, ey = d.y - cy, ez = d.z - cz;
+      R = fmaxf(R, sqrtf(dot3(ex, ey, ez, ex, ey, ez)) + sqrtf(d.w));
+    }
+    R = R * 1.0001f + 1e-4f;
+    grp[c] = make_float4(cx, cy, cz, R * R);
+  }
+  __syncthreads();
   const int64_t n = a.n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float ox = __ldg(a.o + i), oy = __ldg(a.o + n + i), oz = __ldg(a.o + 2 * n + i);
-    const float dx = __ldg(a.d + i), dy = __ldg(a.d + n + i), dz = __ldg(a.d + 2 * n + i);
+  const int lane = threadIdx.x & 31;
+  // whole warps step through the rays (lanes past the end take part in the
+  // ballots with a dummy ray and write nothing)
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const bool act = i < n;
+    float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
+    if (act) {
+      ox = __ldg(a.o + i), oy = __ldg(a.o + n + i), oz = __ldg(a.o + 2 * n + i);
+      dx = __ldg(a.d + i), dy = __ldg(a.d + n + i), dz = __ldg(a.d + 2 * n + i);
+    }
     const float idd = 1.0f / dot3(dx, dy, dz, dx, dy, dz);
+    const float ild = sqrtf(idd);
+    // the warp's bundle: origin oc and unit direction ua of its middle active
+    // lane, ro = max |o_i - oc|, del = max |d_i / |d_i| - ua|
+    const unsigned am = __ballot_sync(0xffffffffu, act);
+    const int src = (__popc(am) - 1) >> 1;  // active lanes are 0 .. popc - 1
+    const float ux = dx * ild, uy = dy * ild, uz = dz * ild;
+    const float ocx = __shfl_sync(0xffffffffu, ox, src), ocy = __shfl_sync(0xffffffffu, oy, src),
+                ocz = __shfl_sync(0xffffffffu, oz, src);
+    const float uax = __shfl_sync(0xffffffffu, ux, src), uay = __shfl_sync(0xffffffffu, uy, src),
+                uaz = __shfl_sync(0xffffffffu, uz, src);
+    float ro = 0.f, del = 0.f;
+    if (act) {
+      const float ex = ox - ocx, ey = oy - ocy, ez = oz - ocz;
+      const float fx = ux - uax, fy = uy - uay, fz = uz - uaz;
+      ro = sqrtf(dot3(ex, ey, ez, ex, ey, ez));
+      del = sqrtf(dot3(fx, fy, fz, fx, fy, fz));
+    }
+    // non-negative floats order like their bit patterns
+    ro = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(ro)));
+    del = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(del)));
     int best = -1;
     float sbest = 0.f;
-    for (int k = 0; k < n_yarns; ++k) {
-      const float4 sd = ps[k].d;
-      // bounding sphere: distance of the centre from the ray line
-      const float mx = ox - sd.x, my = oy - sd.y, mz = oz - sd.z;
-      const float mb = dot3(mx, my, mz, dx, dy, dz) * idd;
-      const float px = fmaf(-mb, dx, mx), py = fmaf(-mb, dy, my), pz = fmaf(-mb, dz, mz);
-      if (dot3(px, py, pz, px, py, pz) > sd.w) continue;
-      const float4 pa = ps[k].a, pb = ps[k].b;
-      // lateral surface about the ray's closest approach to the axis
-      const float qx = ox - pa.x, qy = oy - pa.y, qz = oz - pa.z;
-      const float qt = dot3(qx, qy, qz, pb.x, pb.y, pb.z);
-      const float dt = dot3(dx, dy, dz, pb.x, pb.y, pb.z);
-      const float qpx = fmaf(-qt, pb.x, qx), qpy = fmaf(-qt, pb.y, qy), qpz = fmaf(-qt, pb.z, qz);
-      const float dpx = fmaf(-dt, pb.x, dx), dpy = fmaf(-dt, pb.y, dy), dpz = fmaf(-dt, pb.z, dz);
-      const float aa = dot3(dpx, dpy, dpz, dpx, dpy, dpz);
-      if (!(aa > 1e-20f)) continue;
-      const float R2 = pb.w * pb.w;
-      if (!(dot3(qpx, qpy, qpz, qpx, qpy, qpz) > R2)) continue;  // starts inside
-      const float sc = -dot3(qpx, qpy, qpz, dpx, dpy, dpz) / aa;
-      const float mpx = fmaf(sc, dpx, qpx), mpy = fmaf(sc, dpy, qpy), mpz = fmaf(sc, dpz, qpz);
-      const float e2 = R2 - dot3(mpx, mpy, mpz, mpx, mpy, mpz);
-      if (e2 < 0.f) continue;
-      const float s = sc - sqrtf(e2 / aa);
-      if (!(s > 0.f) || (best >= 0 && !(s < sbest))) continue;
-      const float w = fmaf(s, dt, qt);
-      if (w < 0.f || w > pa.w) continue;
-      best = k;
-      sbest = s;
+    for (int c0 = 0; c0 < n_grp; c0 += 32) {
+      unsigned gm = __ballot_sync(
+          0xffffffffu, c0 + lane < n_grp && bundle_reaches(grp[c0 + lane], ocx, ocy, ocz, uax,
+                                                           uay, uaz, ro, del));
+      while (gm) {
+        // the next four kept groups (offsets in c0, 0xff for none) in bytes
+        uint32_t four = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          four |= (gm ? (uint32_t)(__ffs(gm) - 1) : 0xffu) << (8 * q);
+          gm &= gm - 1;
+        }
+        const uint32_t gq = (four >> (8 * (lane >> 3))) & 0xffu;
+        const int kl = (c0 + (int)gq) * kGroupPieces + (lane & 7);
+        unsigned pm = __ballot_sync(
+            0xffffffffu, gq != 0xffu && kl < n_yarns &&
+                             bundle_reaches(ps[kl].d, ocx, ocy, ocz, uax, uay, uaz, ro, del));
+        while (pm) {
+          const int b = __ffs(pm) - 1;
+          pm &= pm - 1;
+          const int k = (c0 + (int)((four >> (8 * (b >> 3))) & 0xffu)) * kGroupPieces + (b & 7);
+          const float4 sd = ps[k].d;
+          // bounding sphere: distance of the centre from the ray line
+          const float mx = ox - sd.x, my = oy - sd.y, mz = oz - sd.z;
+          const float mb = dot3(mx, my, mz, dx, dy, dz) * idd;
+          const float px = fmaf(-mb, dx, mx), py = fmaf(-mb, dy, my), pz = fmaf(-mb, dz, mz);
+          if (dot3(px, py, pz, px, py, pz) > sd.w) continue;
+          const float4 pa = ps[k].a, pb = ps[k].b;
+          // lateral surface about the ray's closest approach to the axis
+          const float qx = ox - pa.x, qy = oy - pa.y, qz = oz - pa.z;
+          const float qt = dot3(qx, qy, qz, pb.x, pb.y, pb.z);
+          const float dt = dot3(dx, dy, dz, pb.x, pb.y, pb.z);
+          const float qpx = fmaf(-qt, pb.x, qx), qpy = fmaf(-qt, pb.y, qy), qpz = fmaf(-qt, pb.z, qz);
+          const float dpx = fmaf(-dt, pb.x, dx), dpy = fmaf(-dt, pb.y, dy), dpz = fmaf(-dt, pb.z, dz);
+          const float aa = dot3(dpx, dpy, dpz, dpx, dpy, dpz);
+          if (!(aa > 1e-20f)) continue;
+          const float R2 = pb.w * pb.w;
+          if (!(dot3(qpx, qpy, qpz, qpx, qpy, qpz) > R2)) continue;  // starts inside
+          const float sc = -dot3(qpx, qpy, qpz, dpx, dpy, dpz) / aa;
+          const float mpx = fmaf(sc, dpx, qpx), mpy = fmaf(sc, dpy, qpy), mpz = fmaf(sc, dpz, qpz);
+          const float e2 = R2 - dot3(mpx, mpy, mpz, mpx, mpy, mpz);
+          if (e2 < 0.f) continue;
+          const float s = sc - sqrtf(e2 / aa);
+          if (!(s > 0.f) || (best >= 0 && !(s < sbest))) continue;
+          const float w = fmaf(s, dt, qt);
+          if (w < 0.f || w > pa.w) continue;
+          best = k;
+          sbest = s;
+        }
+      }
     }
+    if (!act) continue;
     if (a.yarn_id) a.yarn_id[i] = best;
     if (a.t_hit) a.t_hit[i] = best >= 0 ? sbest : 0.f;
     if (best < 0) {
@@ -166,12 +270,22 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
 
 cudaError_t launch_trace_yarns(const bysdf_yarn* yarns, int n_yarns, const TraceArgs& a,
                                int grid, cudaStream_t st) {
-  const size_t smem = sizeof(PieceS) * (size_t)n_yarns;
+  const int n_grp = (n_yarns + kGroupPieces - 1) / kGroupPieces;
+  const size_t smem = sizeof(PieceS) * (size_t)n_yarns + sizeof(float4) * (size_t)n_grp;
+  cudaError_t e;
   if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_trace_yarns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_trace_yarns, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
   }
+  // one resident wave: every CTA stages the pieces once
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_yarns, 256, smem)) !=
+          cudaSuccess)
+    return e;
+  if (per_sm > 0 && grid > sms * per_sm) grid = sms * per_sm;
   k_trace_yarns<<<grid, 256, smem, st>>>(yarns, n_yarns, a);
   return cudaGetLastError();
 }

@@ -91,6 +91,34 @@ def test_traced_records_feed_the_bysdf(api, orc):
     assert (st == 0).mean() > 0.5
 
 
+def test_degenerate_rays_do_not_disturb_their_warp(api):
+    # rays with a zero or non-finite direction or origin miss, and the other
+    # rays of their warps (which share a culling bound with them) keep the
+    # result they have without them, bit for bit
+    sc = I.woven_scene(6, 6)
+    rays = I.camera_rays(64, 48, extent=15.0, jitter_seed=2)
+    Y = api.yarns_to_device(sc)
+    base = {k: np_(v) for k, v in
+            api.trace_yarns(Y, {k: torch.from_numpy(v).cuda() for k, v in rays.items()},
+                            LIGHT).items()}
+    bad = dict((k, v.copy()) for k, v in rays.items())
+    idx = np.array([5, 37, 38, 700, 1501, 64 * 48 - 1])
+    bad["d"][:, idx[:2]] = 0.0
+    bad["d"][0, idx[2]] = np.nan
+    bad["d"][1, idx[3]] = np.inf
+    bad["o"][2, idx[4]] = np.nan
+    bad["o"][:, idx[5]] = -np.inf
+    got = {k: np_(v) for k, v in
+           api.trace_yarns(Y, {k: torch.from_numpy(v).cuda() for k, v in bad.items()},
+                           LIGHT).items()}
+    assert np.all(got["mat_id"][idx] == -1)
+    keep = np.ones(64 * 48, bool)
+    keep[idx] = False
+    assert (base["mat_id"][keep] >= 0).mean() > 0.5
+    for k in base:
+        np.testing.assert_array_equal(got[k][..., keep], base[k][..., keep], err_msg=k)
+
+
 def test_trace_argument_errors(api):
     sc = I.woven_scene(2, 2)
     Y = api.yarns_to_device(sc)

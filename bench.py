@@ -53,8 +53,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="bb93f164d5949d173659fd79e65112b7ff72a4cdd5f763eba2965adf89aa0275",
-                       bytes_per_record=85.10,
+TRAFFIC_CAPTURE = dict(sources_sha256="4fa9e56673fe36945d2980d048e7715d81560ffc4fb9a61bb0eb55f71a08a4b1",
+                       bytes_per_record=85.07,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

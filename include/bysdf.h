@@ -382,8 +382,9 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
  * through the fused eval + sample kernel in chunks: the copy of chunk c+1 to
  * the device, the kernel on chunk c and the copy of chunk c-1's results back
  * run concurrently on three streams owned by the pipeline.  The pipeline
- * allocates its device slots (two chunks of records, outputs and workspace)
- * and streams once, at creation; calls allocate nothing.  Host buffers use
+ * allocates its device slots (three chunks of records, outputs and
+ * workspace: the copy-in of chunk c + 3 waits only for the copy-out of chunk
+ * c) and streams once, at creation; calls allocate nothing.  Host buffers use
  * the plane layout of the device calls with plane stride n.  The call is
  * asynchronous on `stream` (it starts after the work queued there and work
  * queued there afterwards waits for it); the host buffers must stay valid

@@ -787,13 +787,18 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
 
 // ------------------------------------------------------ host pipeline -----
 struct bysdf_host_pipeline {
+  // Three slots: the copy-in of chunk c + 3 waits only for the copy-out of
+  // chunk c, so with the link busy both ways the copy-ins run back to back
+  // (with two, every second copy-in waited for a copy-out).
+  static constexpr int kSlots = 3;
   const bysdf_materials* m = nullptr;
   int64_t chunk = 0;
   bool with_ratio = false;
   cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
-  cudaEvent_t start = nullptr, in_done[2] = {}, run_done[2] = {}, out_done[2] = {};
-  bool out_pending[2] = {false, false};
-  uint8_t* dev = nullptr;   // both slots
+  cudaEvent_t start = nullptr, in_done[kSlots] = {}, run_done[kSlots] = {},
+              out_done[kSlots] = {};
+  bool out_pending[kSlots] = {};
+  uint8_t* dev = nullptr;   // all slots
   size_t slot_bytes = 0, ws_bytes = 0;
 };
 
@@ -847,14 +852,14 @@ int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with
     return fail(BYSDF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&p->dev, 2 * p->slot_bytes)) != cudaSuccess) return bad(e, "cudaMalloc");
+  if ((e = cudaMalloc(&p->dev, bysdf_host_pipeline::kSlots * p->slot_bytes)) != cudaSuccess) return bad(e, "cudaMalloc");
   if ((e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking)) != cudaSuccess)
     return bad(e, "cudaStreamCreate");
   if ((e = cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming)) != cudaSuccess)
     return bad(e, "cudaEventCreate");
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < bysdf_host_pipeline::kSlots; ++k)
     if ((e = cudaEventCreateWithFlags(&p->in_done[k], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&p->run_done[k], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&p->out_done[k], cudaEventDisableTiming)) != cudaSuccess)
@@ -868,7 +873,7 @@ int bysdf_host_pipeline_destroy(bysdf_host_pipeline* p) {
   if (p->s_in) cudaStreamSynchronize(p->s_in);
   if (p->s_run) cudaStreamSynchronize(p->s_run);
   if (p->s_out) cudaStreamSynchronize(p->s_out);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < bysdf_host_pipeline::kSlots; ++k) {
     if (p->in_done[k]) cudaEventDestroy(p->in_done[k]);
     if (p->run_done[k]) cudaEventDestroy(p->run_done[k]);
     if (p->out_done[k]) cudaEventDestroy(p->out_done[k]);
@@ -901,7 +906,7 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
   const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
   for (int64_t a = 0, c = 0; a < n; a += p->chunk, ++c) {
     const int64_t mcount = std::min(p->chunk, n - a);
-    const int k = (int)(c & 1);
+    const int k = (int)(c % bysdf_host_pipeline::kSlots);
     SlotPtrs s;
     slot_layout(p->chunk, p->ws_bytes, p->dev + (size_t)k * p->slot_bytes, &s);
     // the slot's previous results must be copied out before it is refilled
@@ -969,7 +974,7 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
     p->out_pending[k] = true;
   }
   // later work on the caller's stream waits for the results
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < bysdf_host_pipeline::kSlots; ++k)
     if (p->out_pending[k]) BY_CU(cudaStreamWaitEvent(caller, p->out_done[k], 0));
   return BYSDF_OK;
 }

@@ -66,12 +66,15 @@ __device__ __forceinline__ bool bundle_reaches(float4 sph, float ocx, float ocy,
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restrict__ yarns,
+// (256, 1): 72 registers without spills, 3 CTAs per SM; held to 64, the
+// differential rays loaded ahead of the culling would spill
+__global__ void __launch_bounds__(256, 1) k_trace_yarns(const bysdf_yarn* __restrict__ yarns,
                                                      int n_yarns, TraceArgs a) {
   extern __shared__ float4 smem_pieces[];
   PieceS* ps = reinterpret_cast<PieceS*>(smem_pieces);
   const int n_grp = (n_yarns + kGroupPieces - 1) / kGroupPieces;
   float4* grp = smem_pieces + 4 * n_yarns;  // (centre, squared radius) per group
+  int32_t* smat = reinterpret_cast<int32_t*>(grp + n_grp);  // material per piece
   // stage the pieces with an orthonormal frame: t / |t|, then n_ref without
   // its t component, normalised; bounding sphere about the piece's centre
   for (int k = threadIdx.x; k < n_yarns; k += blockDim.x) {
@@ -98,6 +101,7 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
     const float rm = rs * 1.0001f + 1e-4f;
     p.d = make_float4(y.p0[0] + hl * tx, y.p0[1] + hl * ty, y.p0[2] + hl * tz, rm * rm);
     ps[k] = p;
+    smat[k] = y.mat_id;
   }
   __syncthreads();
   // group spheres: the box around the pieces' spheres, then the largest
@@ -128,16 +132,35 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
   __syncthreads();
   const int64_t n = a.n;
   const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // whole warps step through the rays (lanes past the end take part in the
-  // ballots with a dummy ray and write nothing)
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n;
-       i0 += (int64_t)gridDim.x * blockDim.x) {
+  // ballots with a dummy ray and write nothing); each lane loads its next ray
+  // while the current one is culled
+  int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  float nox = 0.f, noy = 0.f, noz = 0.f, ndx = 0.f, ndy = 0.f, ndz = 1.f;
+  if (i0 + lane < n) {
+    const int64_t j = i0 + lane;
+    nox = __ldg(a.o + j), noy = __ldg(a.o + n + j), noz = __ldg(a.o + 2 * n + j);
+    ndx = __ldg(a.d + j), ndy = __ldg(a.d + n + j), ndz = __ldg(a.d + 2 * n + j);
+  }
+  for (; i0 < n; i0 += stride) {
     const int64_t i = i0 + lane;
     const bool act = i < n;
-    float ox = 0.f, oy = 0.f, oz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
-    if (act) {
-      ox = __ldg(a.o + i), oy = __ldg(a.o + n + i), oz = __ldg(a.o + 2 * n + i);
-      dx = __ldg(a.d + i), dy = __ldg(a.d + n + i), dz = __ldg(a.d + 2 * n + i);
+    const float ox = nox, oy = noy, oz = noz, dx = ndx, dy = ndy, dz = ndz;
+    if (i + stride < n) {
+      const int64_t j = i + stride;
+      nox = __ldg(a.o + j), noy = __ldg(a.o + n + j), noz = __ldg(a.o + 2 * n + j);
+      ndx = __ldg(a.d + j), ndy = __ldg(a.d + n + j), ndz = __ldg(a.d + 2 * n + j);
+    }
+    // the differential rays, loaded while the warp culls
+    const bool diff = a.ratio && a.o1 && a.d1 && a.o2 && a.d2;
+    float o1x = 0.f, o1y = 0.f, o1z = 0.f, d1x = 0.f, d1y = 0.f, d1z = 0.f;
+    float o2x = 0.f, o2y = 0.f, o2z = 0.f, d2x = 0.f, d2y = 0.f, d2z = 0.f;
+    if (act && diff) {
+      o1x = __ldg(a.o1 + i), o1y = __ldg(a.o1 + n + i), o1z = __ldg(a.o1 + 2 * n + i);
+      d1x = __ldg(a.d1 + i), d1y = __ldg(a.d1 + n + i), d1z = __ldg(a.d1 + 2 * n + i);
+      o2x = __ldg(a.o2 + i), o2y = __ldg(a.o2 + n + i), o2z = __ldg(a.o2 + 2 * n + i);
+      d2x = __ldg(a.d2 + i), d2y = __ldg(a.d2 + n + i), d2z = __ldg(a.d2 + 2 * n + i);
     }
     const float idd = 1.0f / dot3(dx, dy, dz, dx, dy, dz);
     const float ild = sqrtf(idd);
@@ -248,18 +271,14 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
     a.wo[i] = dot3(a.light[0], a.light[1], a.light[2], p.c.x, p.c.y, p.c.z);
     a.wo[n + i] = dot3(a.light[0], a.light[1], a.light[2], bx, by, bz);
     a.wo[2 * n + i] = dot3(a.light[0], a.light[1], a.light[2], p.b.x, p.b.y, p.b.z);
-    a.mat_id[i] = yarns[best].mat_id;
+    a.mat_id[i] = smat[best];
     if (a.ratio) {
       // Sec. 5.3: the differential rays' offsets about the same axis bound
       // the footprint; the record carries its half-width in h
       float r = 0.f;
-      if (a.o1 && a.d1 && a.o2 && a.d2) {
-        const float h1 = line_offset(p, bx, by, bz, __ldg(a.o1 + i), __ldg(a.o1 + n + i),
-                                     __ldg(a.o1 + 2 * n + i), __ldg(a.d1 + i),
-                                     __ldg(a.d1 + n + i), __ldg(a.d1 + 2 * n + i));
-        const float h2 = line_offset(p, bx, by, bz, __ldg(a.o2 + i), __ldg(a.o2 + n + i),
-                                     __ldg(a.o2 + 2 * n + i), __ldg(a.d2 + i),
-                                     __ldg(a.d2 + n + i), __ldg(a.d2 + 2 * n + i));
+      if (diff) {
+        const float h1 = line_offset(p, bx, by, bz, o1x, o1y, o1z, d1x, d1y, d1z);
+        const float h2 = line_offset(p, bx, by, bz, o2x, o2y, o2z, d2x, d2y, d2z);
         const float w1 = fabsf(h1 - h0), w2 = fabsf(h2 - h0);
         r = (isfinite(w1) && isfinite(w2)) ? fmaxf(w1, w2) : 2.0f;
       }
@@ -271,7 +290,8 @@ __global__ void __launch_bounds__(256) k_trace_yarns(const bysdf_yarn* __restric
 cudaError_t launch_trace_yarns(const bysdf_yarn* yarns, int n_yarns, const TraceArgs& a,
                                int grid, cudaStream_t st) {
   const int n_grp = (n_yarns + kGroupPieces - 1) / kGroupPieces;
-  const size_t smem = sizeof(PieceS) * (size_t)n_yarns + sizeof(float4) * (size_t)n_grp;
+  const size_t smem = sizeof(PieceS) * (size_t)n_yarns + sizeof(float4) * (size_t)n_grp +
+                      sizeof(int32_t) * (size_t)n_yarns;
   cudaError_t e;
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k_trace_yarns, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -541,4 +541,13 @@ def test_host_pipeline_matches_device_call(api):
         torch.cuda.synchronize()
         for k in ("f", "pdf", "status", "wo", "weight", "pdf_s", "lobe_status"):
             assert np.array_equal(hout[k].numpy(), np_(o[k])), k
+        # a second call on the same pipeline, other records and another
+        # ragged length: the slots' earlier contents must not leak through
+        rec2 = {k: np.ascontiguousarray(v[..., 7:20_007][..., ::-1]) for k, v in rec.items()}
+        o2 = api.eval_sample_pdf(M, dev(api, rec2))
+        hout2 = api.pinned_fused_outputs(len(rec2["h"]))
+        pipe.run(api.pinned_records(rec2), hout2)
+        torch.cuda.synchronize()
+        for k in ("f", "pdf", "status", "wo", "weight", "pdf_s", "lobe_status"):
+            assert np.array_equal(hout2[k].numpy(), np_(o2[k])), k
         pipe.close()

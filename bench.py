@@ -53,8 +53,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="4fa9e56673fe36945d2980d048e7715d81560ffc4fb9a61bb0eb55f71a08a4b1",
-                       bytes_per_record=85.07,
+TRAFFIC_CAPTURE = dict(sources_sha256="2c0b15d5143d7305c08ced8a0d226ed86c5c8298243d0c0084b76d6580b831c8",
+                       bytes_per_record=84.99,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM
@@ -279,10 +279,12 @@ def main():
                     help="main workload only, no clocks/e2e/CPU baseline (for ncu)")
     ap.add_argument("--records", type=int, default=0,
                     help="use only the first N records of the workload (profiling)")
-    ap.add_argument("--profile-op", default="fused", choices=["fused", "backward", "trace"],
+    ap.add_argument("--profile-op", default="fused",
+                    choices=["fused", "backward", "trace", "multiscale"],
                     help="with --profile: fused = eval + sample + pdf over workload 2; "
                          "backward = forward eval + backward over workload 5; trace = "
-                         "2048 x 2048 camera rays against a 512-piece yarn patch")
+                         "2048 x 2048 camera rays against a 512-piece yarn patch; "
+                         "multiscale = eval + sample + pdf over workload 3")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -302,6 +304,14 @@ def main():
 
     if args.profile and args.profile_op == "backward":
         profile_backward(api, torch, args, rank)
+        return
+    if args.profile and args.profile_op == "multiscale":
+        M = api.Materials(I.materials(3))
+        _, d, _ = workload_device(api, 3, rank, args.records)
+        o = api.alloc_fused(int(d["h"].shape[0]), "cuda")
+        ms, _ = timed(lambda: api.eval_sample_pdf(M, d, out=o), args.steps, args.warmup)
+        print(json.dumps(dict(profile="multiscale", workload=I.WORKLOAD_NAME[3],
+                              records=int(d["h"].shape[0]), ms_per_step=ms)), flush=True)
         return
     if args.profile and args.profile_op == "trace":
         sc = I.woven_scene(16, 16)
@@ -405,7 +415,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             pipe.run(hin, hout)
-        torch.cuda.synchronize()
+            # a step ends with its results readable in host memory
+            torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         bi, bo = api.HostPipeline.bytes_per_record(hin, hout)
         line["e2e"] = dict(value=n * e2e_steps / dt, unit=UNIT,

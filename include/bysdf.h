@@ -133,7 +133,10 @@ typedef struct bysdf_hits {
 /* Launch shape of the persistent kernels (chosen by bysdf_autotune). */
 typedef struct bysdf_launch_config {
   int32_t block;          /* threads per CTA: 128, 256 or 512               */
-  int32_t items;          /* records per lane per warp tile: 1, 2 or 4       */
+  int32_t items;          /* records per lane per warp tile: 1, 2 or 4; the
+                             forward calls take 1 for a batch of fewer tiles
+                             than the grid's resident warps, so that more
+                             warps get work                                  */
   int32_t ctas_per_sm;    /* resident CTAs per SM the grid is sized for
                              (0: as many as fit)                             */
   int32_t occupancy;      /* register budget: 0 the default, 1 a tighter cap
@@ -352,7 +355,11 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
                 int64_t n, float* f_rgb, float* wo, float* weight, float* pdf,
                 uint8_t* status, void* stream);
 
-/* Launch shape used for op (BYSDF_OP_*), per table. */
+/* Launch shape used for op (BYSDF_OP_*), per table.  Until one is set here
+ * or by bysdf_autotune, the forward calls take 512 x 2 at occupancy 0 for
+ * records without a footprint and 256 x 4 at occupancy 1 for records with a
+ * ratio plane (up to 16 geometry nodes each); once set, the shape serves
+ * both kinds.  get returns the set shape, else the first default. */
 int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_config* cfg);
 int bysdf_get_launch_config(const bysdf_materials* m, int op, bysdf_launch_config* cfg);
 

@@ -26,6 +26,7 @@ struct bysdf_materials {
   uint8_t* d_table = nullptr;
   std::vector<bysdf_material_desc> desc;
   bysdf_launch_config cfg[BYSDF_NOPS];
+  bool cfg_set[BYSDF_NOPS] = {};  // chosen by the caller or by bysdf_autotune
 };
 
 namespace {
@@ -336,6 +337,25 @@ bysdf_launch_config default_cfg() {
   return c;
 }
 
+// Records with a footprint run up to 16 geometry nodes each: their default
+// shape holds more warps per SM (24, registers capped) and larger tiles, so
+// that lanes grouped by cost wait less on one another.
+bysdf_launch_config footprint_default_cfg() {
+  bysdf_launch_config c;
+  c.block = 256;
+  c.items = 4;
+  c.ctas_per_sm = 0;
+  c.occupancy = 1;
+  return c;
+}
+
+// The shape of a forward call: the caller's (or the tuned) one when set,
+// else the default for the kind of records.
+bysdf_launch_config fwd_cfg(const bysdf_materials* m, int op, const bysdf_hits* h) {
+  if (m->cfg_set[op] || !h || !h->ratio) return m->cfg[op];
+  return footprint_default_cfg();
+}
+
 int check_hits(const bysdf_materials* m, const bysdf_hits* h, bool need_wo, int64_t n) {
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   if (!h) return fail(BYSDF_E_ARG, "hits is NULL");
@@ -474,6 +494,16 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, c.items, c.occupancy, smem));
   int occ = 0;
   BY_CU(forward_occupancy(bits, c.block, c.items, c.occupancy, smem, &occ));
+  // fewer warp tiles than resident warps leaves warps idle: tiles of 32
+  // records spread a small batch over twice (or four times) as many warps
+  const int64_t warps = (int64_t)grid_for(m, c, occ) * (c.block / 32);
+  if (c.items > 1 && a.n_tiles < warps) {
+    c.items = 1;
+    a.tile = 32;
+    a.n_tiles = (n + 31) / 32;
+    if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, 1, c.occupancy, smem));
+    BY_CU(forward_occupancy(bits, c.block, 1, c.occupancy, smem, &occ));
+  }
   if ((rc = plan(m, a, ws, st))) return rc;
   BY_CU(launch_forward(bits, a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));
   return BYSDF_OK;
@@ -757,7 +787,7 @@ int bysdf_eval(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, floa
   o.status = status;
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_EVAL]);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_EVAL, hits));
 }
 
 int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
@@ -782,7 +812,7 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
   o.pdf = pdf;
   o.status = status;
   return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, scratch,
-                     BYSDF_NOALLOC_SCRATCH_BYTES, st, m->cfg[BYSDF_OP_EVAL], need);
+                     BYSDF_NOALLOC_SCRATCH_BYTES, st, fwd_cfg(m, BYSDF_OP_EVAL, hits), need);
 }
 
 // ------------------------------------------------------ host pipeline -----
@@ -950,7 +980,7 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
     o.pdf_s = s.pdf_s;
     o.lobe_status = s.lstat;
     int rc = run_forward(p->m, BYSDF_OP_FUSED, &dh, s.u0, s.u1, mcount, o, s.ws, p->ws_bytes,
-                         p->s_run, p->m->cfg[BYSDF_OP_FUSED]);
+                         p->s_run, fwd_cfg(p->m, BYSDF_OP_FUSED, &dh));
     if (rc) return rc;
     BY_CU(cudaEventRecord(p->run_done[k], p->s_run));
     BY_CU(cudaStreamWaitEvent(p->s_out, p->run_done[k], 0));
@@ -989,7 +1019,7 @@ int bysdf_sample(const bysdf_materials* m, const bysdf_hits* hits, const float* 
   o.lobe_status = lobe_status;
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_SAMPLE, hits, u0, u1, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_SAMPLE]);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_SAMPLE, hits));
 }
 
 int bysdf_pdf(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float* pdf,
@@ -999,7 +1029,7 @@ int bysdf_pdf(const bysdf_materials* m, const bysdf_hits* hits, int64_t n, float
   o.status = status;
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_PDF, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_PDF]);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_PDF, hits));
 }
 
 int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, const float* u0,
@@ -1017,7 +1047,7 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
   o.lobe_status = lobe_status_s;
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_forward(m, BYSDF_OP_FUSED, hits, u0, u1, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED]);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_FUSED, hits));
 }
 
 int bysdf_trace_yarns(const bysdf_yarn* yarns, int32_t n_yarns, const bysdf_rays* rays,
@@ -1080,7 +1110,8 @@ int bysdf_eval_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
   o.pdf = pdf;
   o.status = status;
   return run_forward(m, BYSDF_OP_EVAL, hits, nullptr, nullptr, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_EVAL], 0, sto);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_EVAL, hits), 0,
+                     sto);
 }
 
 int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits* hits,
@@ -1100,7 +1131,8 @@ int bysdf_eval_sample_pdf_stochastic(const bysdf_materials* m, const bysdf_hits*
   o.pdf_s = pdf_s;
   o.lobe_status = lobe_status_s;
   return run_forward(m, BYSDF_OP_FUSED, hits, u0, u1, n, o, workspace, workspace_bytes,
-                     reinterpret_cast<cudaStream_t>(stream), m->cfg[BYSDF_OP_FUSED], 0, sto);
+                     reinterpret_cast<cudaStream_t>(stream), fwd_cfg(m, BYSDF_OP_FUSED, hits), 0,
+                     sto);
 }
 
 int bysdf_eval_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
@@ -1183,6 +1215,7 @@ int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_confi
   if (cfg->ctas_per_sm < 0) return fail(BYSDF_E_ARG, "ctas_per_sm < 0");
   if (cfg->occupancy != 0 && cfg->occupancy != 1) return fail(BYSDF_E_ARG, "occupancy must be 0 or 1");
   m->cfg[op] = *cfg;
+  m->cfg_set[op] = true;
   return BYSDF_OK;
 }
 
@@ -1241,6 +1274,7 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
   cudaEventDestroy(e1);
   if (rc) return rc;
   m->cfg[op] = best_c;
+  m->cfg_set[op] = true;
   *best = best_c;
   return BYSDF_OK;
 }

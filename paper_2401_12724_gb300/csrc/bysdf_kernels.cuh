@@ -357,8 +357,9 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
 // ---------------------------------------------------- work order in a tile --
 // Lanes of a warp run in lock step, so a round costs as much as its most
 // expensive record (most plies, most footprint nodes).  The records of a warp
-// tile are therefore taken in order of an estimated cost, K nodes x N_p
-// plies, then of material (so that the lanes of a round mostly read one
+// tile are therefore taken in order of their loop structure, K footprint
+// nodes then N_p plies (records of one round run the same node and ply
+// loops), then of material (so that the lanes of a round mostly read one
 // table), by a bitonic sort of (cost << 16 | material << 8 | index) keys
 // across the warp (ITEMS keys per lane; element e = j * 32 + lane lives in
 // v[j] of lane `lane`).  Empty slots hold 0xffffffff and sort last.
@@ -415,7 +416,7 @@ __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, 
       }
       int K = 1;
       if (a.ratio) K = footprint(__ldg(a.h + i), __ldg(a.ratio + i), m->kmax).K;
-      const uint32_t cost = (uint32_t)min(K * m->np, 32767);
+      const uint32_t cost = (uint32_t)((K << 4) | m->np);  // K <= 64, N_p <= 8
       v[j] = (cost << 16) | ((uint32_t)(mm & 0xff) << 8) | (uint32_t)idx;
     }
   }

@@ -33,8 +33,10 @@ def np_(t):
     return t.detach().cpu().numpy()
 
 
-def traced(api, orc, n_yarns=6, pieces=6, w=96, h=80):
+def traced(api, orc, n_yarns=6, pieces=6, w=96, h=80, keep=None):
     sc = I.woven_scene(n_yarns, pieces)
+    if keep is not None:
+        sc = sc[:keep]
     rays = I.camera_rays(w, h, extent=pieces * 2.5, jitter_seed=5)
     Y = api.yarns_to_device(sc)
     rd = {k: torch.from_numpy(v).cuda() for k, v in rays.items()}
@@ -43,21 +45,23 @@ def traced(api, orc, n_yarns=6, pieces=6, w=96, h=80):
     return sc, rays, g, o
 
 
-def test_trace_matches_oracle(api, orc):
-    sc, rays, g, o = traced(api, orc)
-    PU.dump("trace", **{"g_" + k: v for k, v in g.items()}, **{"o_" + k: v for k, v in o.items()})
+def check_trace(g, o, min_hit=0.8, extent=15.0):
+    # float32 hit positions carry a few ulp of the camera distance, which the
+    # camera sets in proportion to the patch extent: the tolerances of the
+    # position-derived outputs (u, h, v) grow with it (2e-5 at extent 15)
+    tol = 2e-5 * extent / 15.0
     same = g["yarn_id"] == o["yarn"]
     # ties between pieces meeting at a joint, and grazing rays, may go either
     # way in float32
     assert same.mean() >= 0.995, same.mean()
     hit = same & (o["yarn"] >= 0)
-    assert hit.mean() > 0.8
+    assert hit.mean() > min_hit, hit.mean()
     assert np.all(g["mat_id"][hit] == o["mat_id"][hit])
     du = np.abs(np.angle(np.exp(1j * (g["u"][hit] - o["u"][hit]))))
-    assert np.quantile(du, 0.999) < 2e-5 and du.max() < 1e-3, du.max()
+    assert np.quantile(du, 0.999) < tol and du.max() < 1e-3, (np.quantile(du, 0.999), du.max())
     dh = np.abs(g["h"][hit] - o["h"][hit])
-    assert np.quantile(dh, 0.999) < 2e-5 and dh.max() < 1e-3, dh.max()
-    np.testing.assert_allclose(g["v"][hit], o["v"][hit], rtol=1e-6, atol=2e-5)
+    assert np.quantile(dh, 0.999) < tol and dh.max() < 1e-3, (np.quantile(dh, 0.999), dh.max())
+    np.testing.assert_allclose(g["v"][hit], o["v"][hit], rtol=1e-6, atol=tol)
     np.testing.assert_allclose(g["wi"][:, hit], o["wi"][:, hit], atol=2e-6)
     np.testing.assert_allclose(g["wo"][:, hit], o["wo"][:, hit], atol=2e-6)
     np.testing.assert_allclose(g["t_hit"][hit], o["t_hit"][hit], rtol=1e-5)
@@ -65,6 +69,22 @@ def test_trace_matches_oracle(api, orc):
     assert np.quantile(dr, 0.999) < 1e-4 + 1e-3 * np.quantile(o["ratio"][hit], 0.999)
     miss = same & (o["yarn"] < 0)
     assert np.all(g["mat_id"][miss] == -1)
+
+
+def test_trace_matches_oracle(api, orc):
+    sc, rays, g, o = traced(api, orc)
+    PU.dump("trace", **{"g_" + k: v for k, v in g.items()}, **{"o_" + k: v for k, v in o.items()})
+    check_trace(g, o)
+
+
+@pytest.mark.parametrize("keep", [2048, 1001])
+def test_trace_max_and_ragged_piece_counts(api, orc, keep):
+    # the largest scene the kernel takes (2048 pieces: 8 rounds of 32 groups)
+    # and a count that ends in a partial group and a partial round of groups
+    sc, rays, g, o = traced(api, orc, n_yarns=32, pieces=32, w=72, h=64, keep=keep)
+    assert len(sc) == keep
+    # the first 1001 pieces are warp yarns only: gaps between them
+    check_trace(g, o, min_hit=0.8 if keep == 2048 else 0.3, extent=32 * 2.5)
 
 
 def test_traced_records_feed_the_bysdf(api, orc):
@@ -127,6 +147,9 @@ def test_trace_argument_errors(api):
         api.trace_yarns(Y, rays, (1.0, 1.0, 0.0))
     with pytest.raises(RuntimeError, match="yarns"):
         api.trace_yarns(Y[:0], rays, LIGHT)
+    big = api.yarns_to_device(I.woven_scene(32, 33))
+    with pytest.raises(RuntimeError, match="2048"):
+        api.trace_yarns(big[:2049], rays, LIGHT)
     partial = dict(rays)
     partial.pop("d2")
     with pytest.raises(RuntimeError, match="differential"):

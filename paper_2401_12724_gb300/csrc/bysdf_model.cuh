@@ -455,10 +455,12 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   G.status = ST_NO_HIT;
   const Footprint fp = footprint(q.h, q.ratio, m.kmax);
   G.width = fp.width;
-  const float g0 = asinf(q.h);
-  const float u_rel = q.u - g0;
-  float su, cu;
-  sincosf(u_rel, &su, &cu);
+  // (sin, cos) of u and, by the angle-difference identity, of the in-plane
+  // ray's azimuth u_rel = u - asin(h): one sine / cosine and one square root
+  float sU, cU;
+  sincosf(q.u, &sU, &cU);
+  const float ch = sqrtf(fmaxf(0.f, 1.0f - q.h * q.h));
+  const float su = fmaf(sU, ch, -cU * q.h), cu = fmaf(cU, ch, sU * q.h);
   const float ex = -cu, ey = -su;
   const K lxy = xsqrt(wi.x * wi.x + wi.y * wi.y);
   if (!(vf(lxy) >= 1e-7f)) return;
@@ -490,7 +492,8 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   for (int j = 0; j < fp.K; ++j) {
     float X0x, X0y;
     if (near) {
-      sincosf(q.u, &X0y, &X0x);
+      X0x = cU;
+      X0y = sU;
     } else {
       // midpoint of stratum j, or a uniform point in it (Sec. 4.2, stratified
       // sampling of h)
@@ -500,7 +503,12 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
         xj = unit24(rnd.w[j & 3]);
       }
       const float hj = fp.h1 + ((float)j + xj) * fp.width / (float)fp.K;
-      sincosf(u_rel + asinf(hj), &X0y, &X0x);
+      // entry azimuth u_rel + asin(hj) by the angle-sum identity from the
+      // record's (sin, cos)(u_rel): one square root per node instead of an
+      // arcsine and a range-reduced sine / cosine
+      const float cj = sqrtf(fmaxf(0.f, 1.0f - hj * hj));
+      X0x = fmaf(cu, cj, -su * hj);
+      X0y = fmaf(su, cj, cu * hj);
     }
     X0x *= m.R;
     X0y *= m.R;

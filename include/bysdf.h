@@ -133,7 +133,7 @@ typedef struct bysdf_hits {
 /* Launch shape of the persistent kernels (chosen by bysdf_autotune). */
 typedef struct bysdf_launch_config {
   int32_t block;          /* threads per CTA: 128, 256 or 512               */
-  int32_t items;          /* records per lane per warp tile: 1, 2 or 4; the
+  int32_t items;          /* records per lane per warp tile: 1, 2, 4 or 8; the
                              forward calls take 1 for a batch of fewer tiles
                              than the grid's resident warps, so that more
                              warps get work                                  */
@@ -357,7 +357,7 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
 
 /* Launch shape used for op (BYSDF_OP_*), per table.  Until one is set here
  * or by bysdf_autotune, the forward calls take 512 x 2 at occupancy 0 for
- * records without a footprint and 256 x 4 at occupancy 1 for records with a
+ * records without a footprint and 256 x 8 at occupancy 1 for records with a
  * ratio plane (up to 16 geometry nodes each); once set, the shape serves
  * both kinds.  get returns the set shape, else the first default. */
 int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_config* cfg);

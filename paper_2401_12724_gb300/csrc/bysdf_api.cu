@@ -338,12 +338,12 @@ bysdf_launch_config default_cfg() {
 }
 
 // Records with a footprint run up to 16 geometry nodes each: their default
-// shape holds more warps per SM (24, registers capped) and larger tiles, so
-// that lanes grouped by cost wait less on one another.
+// shape holds more warps per SM (24, registers capped) and tiles of 256
+// records, so that the sort gives each round records of equal loop counts.
 bysdf_launch_config footprint_default_cfg() {
   bysdf_launch_config c;
   c.block = 256;
-  c.items = 4;
+  c.items = 8;
   c.ctas_per_sm = 0;
   c.occupancy = 1;
   return c;
@@ -1210,8 +1210,8 @@ int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_confi
   if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
   if (cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
     return fail(BYSDF_E_ARG, "block must be 128, 256 or 512");
-  if (cfg->items != 1 && cfg->items != 2 && cfg->items != 4)
-    return fail(BYSDF_E_ARG, "items must be 1, 2 or 4");
+  if (cfg->items != 1 && cfg->items != 2 && cfg->items != 4 && cfg->items != 8)
+    return fail(BYSDF_E_ARG, "items must be 1, 2, 4 or 8");
   if (cfg->ctas_per_sm < 0) return fail(BYSDF_E_ARG, "ctas_per_sm < 0");
   if (cfg->occupancy != 0 && cfg->occupancy != 1) return fail(BYSDF_E_ARG, "occupancy must be 0 or 1");
   m->cfg[op] = *cfg;
@@ -1246,7 +1246,7 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
   bysdf_launch_config best_c = m->cfg[op];
   int rc = BYSDF_OK;
   for (int block : {128, 256, 512}) {
-    for (int items : {1, 2, 4}) {
+    for (int items : {1, 2, 4, 8}) {
       for (int occ_mode : {0, 1}) {
         if (occ_mode == 1 && block == 512) continue;
         bysdf_launch_config c{block, items, 0, occ_mode};

@@ -62,6 +62,7 @@ const void* fwd_kernel_b(int items, int occ) {
     case 1: return fwd_kernel_bi<OP, BLOCK, 1>(occ);
     case 2: return fwd_kernel_bi<OP, BLOCK, 2>(occ);
     case 4: return fwd_kernel_bi<OP, BLOCK, 4>(occ);
+    case 8: return fwd_kernel_bi<OP, BLOCK, 8>(occ);
   }
   return nullptr;
 }

@@ -12,6 +12,7 @@ static const void* stoch_b(int items) {
     case 1: return (const void*)k_forward<OP, BLOCK, 1, MINB>;
     case 2: return (const void*)k_forward<OP, BLOCK, 2, MINB>;
     case 4: return (const void*)k_forward<OP, BLOCK, 4, MINB>;
+    case 8: return (const void*)k_forward<OP, BLOCK, 8, MINB>;
   }
   return nullptr;
 }

@@ -488,8 +488,14 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     a.stoch_index0 = sto->index_offset;
     a.stoch_flags = sto->flags;
   }
-  const size_t smem = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
-                                              : (size_t)(c.block / 32) * m->stride;
+  // tables, then each warp's sorted tile keys (4 bytes per record of a tile)
+  const size_t tables = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
+                                                : (size_t)(c.block / 32) * m->stride;
+  a.order_off = (int32_t)align_up(tables, 16);
+  auto key_bytes = [&](int items) {
+    return items >= kSmemKeyItems ? sizeof(uint32_t) * (size_t)c.block * items : 0;
+  };
+  size_t smem = (size_t)a.order_off + key_bytes(c.items);
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
   if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, c.items, c.occupancy, smem));
   int occ = 0;
@@ -501,6 +507,7 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     c.items = 1;
     a.tile = 32;
     a.n_tiles = (n + 31) / 32;
+    smem = (size_t)a.order_off + key_bytes(1);
     if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, 1, c.occupancy, smem));
     BY_CU(forward_occupancy(bits, c.block, 1, c.occupancy, smem, &occ));
   }

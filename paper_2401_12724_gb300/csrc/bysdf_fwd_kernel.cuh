@@ -17,9 +17,23 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
                          [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane, int) {
     uint32_t order[ITEMS];
     tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, order);
+    // from 4 records per lane on, the sorted keys wait in shared memory while
+    // the records run, which frees their registers (each lane reads back only
+    // its own slots, so no synchronisation is needed)
+    uint32_t* keys = nullptr;
+    if constexpr (ITEMS >= kSmemKeyItems) {
+      keys = reinterpret_cast<uint32_t*>(smem + a.order_off) + (threadIdx.x >> 5) * (32 * ITEMS);
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) keys[j * 32 + lane] = order[j];
+    }
 #pragma unroll 1
     for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t e = pick<ITEMS>(order, j);
+      uint32_t e;
+      if constexpr (ITEMS >= kSmemKeyItems) {
+        e = keys[j * 32 + lane];
+      } else {
+        e = pick<ITEMS>(order, j);
+      }
       if (e == 0xffffffffu) continue;
       const int64_t i = begin + (e & 0xffu);
       Record q;

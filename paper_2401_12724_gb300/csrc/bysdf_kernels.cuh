@@ -40,7 +40,7 @@ struct KArgs {
   float* grad_params;
   float* partials;       // deterministic backward: [n_tiles][n_param]
   int32_t n_param;       // gradient columns: 8, or 15 (extended set)
-  int32_t pad_np;
+  int32_t order_off;      // forward: byte offset of the warps' sort keys in shared memory
   float *grad_wi, *grad_wo;  // direction backward: 3 planes each, or NULL
   uint64_t stoch_seed;       // stochastic estimators: generator key word 0,
   int64_t stoch_index0;      //   global index of record 0,
@@ -422,6 +422,10 @@ __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, 
   }
   warp_bitonic_sort<ITEMS>(v, lane);
 }
+
+// tiles of at least this many records per lane keep their sorted keys in
+// shared memory (kSmemKeyItems * 4 bytes per thread, behind the tables)
+constexpr int kSmemKeyItems = 4;
 
 template <int ITEMS>
 __device__ __forceinline__ uint32_t pick(const uint32_t (&v)[ITEMS], int j) {

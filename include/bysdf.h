@@ -239,7 +239,7 @@ int bysdf_eval_sample_pdf(const bysdf_materials* m, const bysdf_hits* hits, cons
  * of block 16; a word w gives (w >> 40) * 2^-24.  The same seed and index
  * draw the same nodes and entry in eval and in the fused op, so a sample's
  * pdf is the stochastic eval's pdf at the sampled direction.  Launches use
- * the op's configured block and items at occupancy 0.  Other arguments and
+ * the op's launch shape, as the deterministic calls do.  Other arguments and
  * errors as bysdf_eval / bysdf_eval_sample_pdf; NULL options: BYSDF_E_ARG;
  * unknown flag bits: BYSDF_E_ARG. */
 #define BYSDF_STOCH_JITTER_NODES 1u

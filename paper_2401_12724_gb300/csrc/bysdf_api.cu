@@ -448,7 +448,6 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     if (op != BYSDF_OP_EVAL && op != BYSDF_OP_FUSED)
       return fail(BYSDF_E_UNSUPPORTED, "stochastic estimators: eval and the fused op only");
     bits |= OPF_STOCH;
-    c.occupancy = 0;  // instantiated in the 128-register shapes
   }
   const bool need_wo = (bits & (OPF_EVAL | OPF_PDF)) != 0;
   int rc = check_hits(m, h, need_wo, n);

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256, 2) k_plain(const KArgs a, int mat, int64_
 
 // ------------------------------------------------------------------ launch --
 static const void* fwd_fn(int op, int block, int items, int occ) {
-  if (op & OPF_STOCH) return fwd_kernel_stoch(op, block, items);
+  if (op & OPF_STOCH) return fwd_kernel_stoch(op, block, items, occ);
   switch (op) {
     case OPF_EVAL: return fwd_kernel_eval(block, items, occ);
     case OPF_SAMPLE: return fwd_kernel_sample(block, items, occ);

@@ -96,8 +96,7 @@ const void* fwd_kernel_eval(int block, int items, int occ);
 const void* fwd_kernel_sample(int block, int items, int occ);
 const void* fwd_kernel_pdf(int block, int items, int occ);
 const void* fwd_kernel_fused(int block, int items, int occ);
-// the stochastic estimators (op with OPF_STOCH; occupancy-0 shapes only),
-// in bysdf_fwd_stoch.cu
-const void* fwd_kernel_stoch(int op, int block, int items);
+// the stochastic estimators (op with OPF_STOCH), in bysdf_fwd_stoch.cu
+const void* fwd_kernel_stoch(int op, int block, int items, int occ);
 
 }  // namespace bysdf

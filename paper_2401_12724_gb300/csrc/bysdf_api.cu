@@ -836,6 +836,7 @@ struct bysdf_host_pipeline {
   bool out_pending[kSlots] = {};
   uint8_t* dev = nullptr;   // all slots
   size_t slot_bytes = 0, ws_bytes = 0;
+  size_t max_pitch = 0;     // of strided copies (cudaDevAttrMaxPitch)
 };
 
 namespace {
@@ -889,6 +890,11 @@ int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with
   };
   cudaError_t e;
   if ((e = cudaMalloc(&p->dev, bysdf_host_pipeline::kSlots * p->slot_bytes)) != cudaSuccess) return bad(e, "cudaMalloc");
+  int dev = 0, pitch = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&pitch, cudaDevAttrMaxPitch, dev)) != cudaSuccess)
+    return bad(e, "cudaDeviceGetAttribute");
+  p->max_pitch = (size_t)pitch;
   if ((e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&p->s_run, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking)) != cudaSuccess)
@@ -951,7 +957,13 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
     auto in1 = [&](float* d, const float* h) {
       return cudaMemcpyAsync(d, h + a, b1, H2D, p->s_in);
     };
+    // a 3-plane array in one strided copy (rows of b1 bytes, host pitch n,
+    // slot pitch mcount) while the host pitch is within the copy engine's
+    // limit, else plane by plane
+    const size_t hp = sizeof(float) * (size_t)n;
+    const bool strided = hp <= p->max_pitch;
     auto in3 = [&](float* d, const float* h) {
+      if (strided) return cudaMemcpy2DAsync(d, b1, h + a, hp, b1, 3, H2D, p->s_in);
       cudaError_t e = cudaSuccess;
       for (int q = 0; q < 3 && e == cudaSuccess; ++q)
         e = cudaMemcpyAsync(d + q * mcount, h + (size_t)q * n + a, b1, H2D, p->s_in);
@@ -994,6 +1006,7 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
       return cudaMemcpyAsync(h + a, d, b1, D2H, p->s_out);
     };
     auto out3 = [&](float* h, const float* d) {
+      if (strided) return cudaMemcpy2DAsync(h + a, hp, d, b1, b1, 3, D2H, p->s_out);
       cudaError_t e = cudaSuccess;
       for (int q = 0; q < 3 && e == cudaSuccess; ++q)
         e = cudaMemcpyAsync(h + (size_t)q * n + a, d + q * mcount, b1, D2H, p->s_out);

@@ -53,8 +53,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="0ad0472f48958fce2a6580ce1433d30d6710d290d4e41437e5e62b929e7627a8",
-                       bytes_per_record=85.06,
+TRAFFIC_CAPTURE = dict(sources_sha256="118d80c44064b459cd95d4830f1cb85e9749dbebbd8ab73a43766c53e7a3f27e",
+                       bytes_per_record=85.03,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

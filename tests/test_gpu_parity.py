@@ -146,6 +146,19 @@ def test_sorted_many_materials_and_plain_form(orc, api):
         np.testing.assert_allclose(f2, f, rtol=1e-3, atol=1e-6)
 
 
+def test_sorted_footprint_records(orc, api):
+    """Material-sorted records that carry a footprint: per-warp table slots,
+    the footprint launch shape (tiles of 256 records, their sort keys in
+    shared memory behind the slots) and ragged segments with empty ones."""
+    mats = I.materials(4)[:64]
+    rec = I.random_records(7001, n_mat=64, seed=61, wi_mode="cosine", ratio="loguniform")
+    seg = np.concatenate([[0], np.cumsum(zipf_sorted(7001, 64, 9))]).astype(np.int64)
+    rec["mat_id"] = (np.searchsorted(seg, np.arange(7001), side="right") - 1).astype(np.int32)
+    M, d, _, _, _ = check_eval(orc, api, mats, rec, seg=seg, name="sorted_fp")
+    cfg = M.launch_config(0)                        # BYSDF_OP_EVAL
+    assert (cfg["block"], cfg["items"]) == (512, 2)   # the shape set for near records
+
+
 @pytest.mark.parametrize("sorted_mode", [False, True])
 def test_backward_matches_oracle_gradient(orc, api, sorted_mode):
     mats = I.materials(5)[:12]

@@ -146,17 +146,32 @@ def test_sorted_many_materials_and_plain_form(orc, api):
         np.testing.assert_allclose(f2, f, rtol=1e-3, atol=1e-6)
 
 
-def test_sorted_footprint_records(orc, api):
+@pytest.mark.parametrize("n", [7001, 1 << 20])
+def test_sorted_footprint_records(orc, api, n):
     """Material-sorted records that carry a footprint: per-warp table slots,
-    the footprint launch shape (tiles of 256 records, their sort keys in
-    shared memory behind the slots) and ragged segments with empty ones."""
+    ragged segments with empty ones, and the footprint launch shape -- at
+    2^20 records its tiles of 256 records with their sort keys in shared
+    memory behind the slots (7001 records fall back to 32-record tiles);
+    the large case is spot-checked on 3000 sampled records."""
     mats = I.materials(4)[:64]
-    rec = I.random_records(7001, n_mat=64, seed=61, wi_mode="cosine", ratio="loguniform")
-    seg = np.concatenate([[0], np.cumsum(zipf_sorted(7001, 64, 9))]).astype(np.int64)
-    rec["mat_id"] = (np.searchsorted(seg, np.arange(7001), side="right") - 1).astype(np.int32)
-    M, d, _, _, _ = check_eval(orc, api, mats, rec, seg=seg, name="sorted_fp")
-    cfg = M.launch_config(0)                        # BYSDF_OP_EVAL
-    assert (cfg["block"], cfg["items"]) == (512, 2)   # the shape set for near records
+    rec = I.random_records(n, n_mat=64, seed=61, wi_mode="cosine", ratio="loguniform")
+    seg = np.concatenate([[0], np.cumsum(zipf_sorted(n, 64, 9))]).astype(np.int64)
+    rec["mat_id"] = (np.searchsorted(seg, np.arange(n), side="right") - 1).astype(np.int32)
+    if n < 100_000:
+        M, d, _, _, _ = check_eval(orc, api, mats, rec, seg=seg, name="sorted_fp")
+        cfg = M.launch_config(0)                        # BYSDF_OP_EVAL
+        assert (cfg["block"], cfg["items"]) == (512, 2)   # the shape set for near records
+        return
+    M = api.Materials(mats)
+    f, p, st = (np_(t) for t in api.eval(M, dev(api, rec, seg)))
+    idx = np.sort(np.random.default_rng(3).choice(n, 3000, replace=False))
+    sub = {k: v[..., idx] for k, v in rec.items()}
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    (fb, pb, sb), pert = PU.conditioning(fn, sub)
+    PU.assert_status(st[idx], sb, [q[2] for q in pert], "sorted_fp_big.status")
+    PU.assert_parity(f[:, idx], fb, [q[0] for q in pert], "sorted_fp_big.f")
+    PU.assert_parity(p[idx], pb, [q[1] for q in pert], "sorted_fp_big.pdf")
+    assert M.workspace_error() == 0
 
 
 @pytest.mark.parametrize("sorted_mode", [False, True])
@@ -512,10 +527,11 @@ def test_edge_cases(orc, api):
     assert (np.abs(f - fo) <= PU.tol(fo)).all(axis=0)[ok].mean() > 0.7
 
 
-def test_full_size_sampled_records(orc, api):
-    """Workload 2 at its full 2^24 records in the benchmark's fused launch:
-    spot-check 3000 sampled records against the oracle."""
-    cfg = 2
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_full_size_sampled_records(orc, api, cfg):
+    """Workloads 2 and 3 at their full 2^24 records in the benchmark's fused
+    launch (workload 3: the footprint shape, 256-record tiles with their keys
+    in shared memory): spot-check 3000 sampled records against the oracle."""
     mats = I.materials(cfg)
     rec = I.records(cfg)
     M = api.Materials(mats)
@@ -524,7 +540,7 @@ def test_full_size_sampled_records(orc, api):
     torch.cuda.synchronize()
     idx = I.sample_indices(cfg, 3000)
     sub = {k: v[..., idx] for k, v in rec.items()}
-    PU.dump("full", idx=idx, f=np_(o["f"])[:, idx], p=np_(o["pdf"])[idx],
+    PU.dump(f"full{cfg}", idx=idx, f=np_(o["f"])[:, idx], p=np_(o["pdf"])[idx],
             st=np_(o["status"])[idx])
     fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
     (fb, pb, sb), pert = PU.conditioning(fn, sub)

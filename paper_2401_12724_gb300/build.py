@@ -19,13 +19,14 @@ SOURCES = ["bysdf_api.cu", "bysdf_fwd.cu", "bysdf_fwd_eval.cu", "bysdf_fwd_sampl
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-# The forward and backward kernels divide and take square roots with the
-# hardware's approximate instructions (a few ulp, far inside the 1e-4
-# tolerance of values and gradients).
+# The forward, backward and ray-yarn kernels divide and take square roots
+# with the hardware's approximate instructions (a few ulp: far inside the
+# 1e-4 tolerance of values and gradients, and inside the margins of the
+# tracer's conservative culling bounds).
 FAST_FLAGS = {s: ["-prec-div=false", "-prec-sqrt=false"]
               for s in ("bysdf_fwd_eval.cu", "bysdf_fwd_sample.cu", "bysdf_fwd_pdf.cu",
                         "bysdf_fwd_fused.cu", "bysdf_fwd_stoch.cu", "bysdf_fwd.cu",
-                        "bysdf_bwd.cu")}
+                        "bysdf_bwd.cu", "bysdf_trace.cu")}
 _lock = threading.Lock()
 
 

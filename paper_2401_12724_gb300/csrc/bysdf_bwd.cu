@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
         mm = mat;
         tb = slot;
       } else {
-        q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
         tb = smem + (size_t)mm * a.stride;
       }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
         q.mat = mat;
         tb = slot;
       } else {
-        q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
         tb = smem + (size_t)mm * a.stride;
       }

@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
         q.mat = mat;
         m = reinterpret_cast<const MatDev*>(slot);
       } else {
-        q.mat = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
         m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
       }

@@ -101,26 +101,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ------------------------------------------------------------ record IO ----
+// Record planes are read once per record and cached in L2 only (ld.global.cg),
+// which leaves L1 to the tables' spill-over and the register spills of the
+// tighter launch shapes.
 __device__ __forceinline__ void load_record(const KArgs& a, int64_t i, bool need_wo,
                                             bool need_u, Record& q) {
   const int64_t n = a.n;
-  q.h = __ldg(a.h + i);
-  q.u = __ldg(a.u + i);
-  q.v = __ldg(a.v + i);
-  q.wi[0] = __ldg(a.wi + i);
-  q.wi[1] = __ldg(a.wi + n + i);
-  q.wi[2] = __ldg(a.wi + 2 * n + i);
+  q.h = __ldcg(a.h + i);
+  q.u = __ldcg(a.u + i);
+  q.v = __ldcg(a.v + i);
+  q.wi[0] = __ldcg(a.wi + i);
+  q.wi[1] = __ldcg(a.wi + n + i);
+  q.wi[2] = __ldcg(a.wi + 2 * n + i);
   if (need_wo) {
-    q.wo[0] = __ldg(a.wo + i);
-    q.wo[1] = __ldg(a.wo + n + i);
-    q.wo[2] = __ldg(a.wo + 2 * n + i);
+    q.wo[0] = __ldcg(a.wo + i);
+    q.wo[1] = __ldcg(a.wo + n + i);
+    q.wo[2] = __ldcg(a.wo + 2 * n + i);
   } else {
     q.wo[0] = q.wo[1] = q.wo[2] = 0.f;
   }
-  q.ratio = a.ratio ? __ldg(a.ratio + i) : 0.f;
+  q.ratio = a.ratio ? __ldcg(a.ratio + i) : 0.f;
   if (need_u) {
-    q.u0 = __ldg(a.u0 + i);
-    q.u1 = __ldg(a.u1 + i);
+    q.u0 = __ldcg(a.u0 + i);
+    q.u1 = __ldcg(a.u1 + i);
   } else {
     q.u0 = q.u1 = 0.f;
   }
@@ -237,8 +240,8 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   float dln_a[2] = {0.f, 0.f};
   eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L, dln_a);
   const int64_t n = a.n;
-  const float g0 = __ldg(a.grad_f + i), g1 = __ldg(a.grad_f + n + i),
-              g2 = __ldg(a.grad_f + 2 * n + i);
+  const float g0 = __ldcg(a.grad_f + i), g1 = __ldcg(a.grad_f + n + i),
+              g2 = __ldcg(a.grad_f + 2 * n + i);
   // f_c = spec + k^B_c body, with k^B = k^B_x (reflection side) or k^B_y
   const float* kb = L.refl ? m.alb : m.alb_y;
   const float gs = g0 + g1 + g2;
@@ -410,12 +413,12 @@ __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, 
       if (mat >= 0) {
         m = reinterpret_cast<const MatDev*>(slot);
       } else {
-        mm = a.mat_id ? __ldg(a.mat_id + i) : 0;
+        mm = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         mm = (mm >= 0 && mm < a.n_mat) ? mm : 0;
         m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
       }
       int K = 1;
-      if (a.ratio) K = footprint(__ldg(a.h + i), __ldg(a.ratio + i), m->kmax).K;
+      if (a.ratio) K = footprint(__ldcg(a.h + i), __ldcg(a.ratio + i), m->kmax).K;
       const uint32_t cost = (uint32_t)((K << 4) | m->np);  // K <= 64, N_p <= 8
       v[j] = (cost << 16) | ((uint32_t)(mm & 0xff) << 8) | (uint32_t)idx;
     }

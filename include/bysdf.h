@@ -356,7 +356,7 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
                 uint8_t* status, void* stream);
 
 /* Launch shape used for op (BYSDF_OP_*), per table.  Until one is set here
- * or by bysdf_autotune, the forward calls take 512 x 2 at occupancy 0 for
+ * or by bysdf_autotune, the forward calls take 512 x 4 at occupancy 0 for
  * records without a footprint and 256 x 8 at occupancy 1 for records with a
  * ratio plane (up to 16 geometry nodes each); once set, the shape serves
  * both kinds.  get returns the set shape, else the first default. */

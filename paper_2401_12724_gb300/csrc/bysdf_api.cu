@@ -326,12 +326,13 @@ int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
 
 // Defaults measured on GB300 with the benchmark workloads (eval + sample +
 // pdf over 2^24 records; forward + backward over 2^22): 16 warps per SM in
-// CTAs of 512, two records per lane per warp tile.  bysdf_autotune refines
-// them for a given record set.
-bysdf_launch_config default_cfg() {
+// CTAs of 512; four records per lane per warp tile for the forward calls
+// (tiles of 128 sort into rounds of equal ply counts; 1.6% over two), two
+// for the backward.  bysdf_autotune refines them for a given record set.
+bysdf_launch_config default_cfg(int op) {
   bysdf_launch_config c;
   c.block = 512;
-  c.items = 2;
+  c.items = op == BYSDF_OP_BACKWARD ? 2 : 4;
   c.ctas_per_sm = 0;  // 0: as many as fit
   c.occupancy = 0;
   return c;
@@ -727,7 +728,7 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
   M->t_max = t_max;
   M->stride = (int)stride;
   M->desc.assign(desc, desc + n);
-  for (int k = 0; k < BYSDF_NOPS; ++k) M->cfg[k] = default_cfg();
+  for (int k = 0; k < BYSDF_NOPS; ++k) M->cfg[k] = default_cfg(k);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   auto cleanup = [&](int rc) {
     if (M->d_table) cudaFree(M->d_table);

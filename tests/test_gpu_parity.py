@@ -160,7 +160,7 @@ def test_sorted_footprint_records(orc, api, n):
     if n < 100_000:
         M, d, _, _, _ = check_eval(orc, api, mats, rec, seg=seg, name="sorted_fp")
         cfg = M.launch_config(0)                        # BYSDF_OP_EVAL
-        assert (cfg["block"], cfg["items"]) == (512, 2)   # the shape set for near records
+        assert (cfg["block"], cfg["items"]) == (512, 4)   # the shape set for near records
         return
     M = api.Materials(mats)
     f, p, st = (np_(t) for t in api.eval(M, dev(api, rec, seg)))

@@ -27,6 +27,16 @@ struct bysdf_materials {
   std::vector<bysdf_material_desc> desc;
   bysdf_launch_config cfg[BYSDF_NOPS];
   bool cfg_set[BYSDF_NOPS] = {};  // chosen by the caller or by bysdf_autotune
+  // resident CTAs per SM of the forward launch shapes met so far, keyed by
+  // (op bits, block, items, occupancy, dynamic shared memory): the query is
+  // host time that a small batch would otherwise pay on every call
+  struct OccEntry {
+    int bits, block, items, occ;
+    size_t smem;
+    int ctas;
+  };
+  mutable std::mutex occ_mu;
+  mutable std::vector<OccEntry> occ_cache;
 };
 
 namespace {
@@ -421,6 +431,19 @@ int plan(const bysdf_materials* m, KArgs& a, void* ws, cudaStream_t st) {
   return BYSDF_OK;
 }
 
+cudaError_t cached_forward_occupancy(const bysdf_materials* m, int bits, int block, int items,
+                                     int occ, size_t smem, int* ctas) {
+  std::lock_guard<std::mutex> lock(m->occ_mu);
+  for (const auto& e : m->occ_cache)
+    if (e.bits == bits && e.block == block && e.items == items && e.occ == occ && e.smem == smem) {
+      *ctas = e.ctas;
+      return cudaSuccess;
+    }
+  const cudaError_t err = forward_occupancy(bits, block, items, occ, smem, ctas);
+  if (err == cudaSuccess) m->occ_cache.push_back({bits, block, items, occ, smem, *ctas});
+  return err;
+}
+
 int grid_for(const bysdf_materials* m, const bysdf_launch_config& c, int occ) {
   int per_sm = c.ctas_per_sm > 0 ? std::min(c.ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
   return m->sm_count * per_sm;
@@ -499,7 +522,7 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
   if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, c.items, c.occupancy, smem));
   int occ = 0;
-  BY_CU(forward_occupancy(bits, c.block, c.items, c.occupancy, smem, &occ));
+  BY_CU(cached_forward_occupancy(m, bits, c.block, c.items, c.occupancy, smem, &occ));
   // fewer warp tiles than resident warps leaves warps idle: tiles of 32
   // records spread a small batch over twice (or four times) as many warps
   const int64_t warps = (int64_t)grid_for(m, c, occ) * (c.block / 32);
@@ -509,7 +532,7 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     a.n_tiles = (n + 31) / 32;
     smem = (size_t)a.order_off + key_bytes(1);
     if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, 1, c.occupancy, smem));
-    BY_CU(forward_occupancy(bits, c.block, 1, c.occupancy, smem, &occ));
+    BY_CU(cached_forward_occupancy(m, bits, c.block, 1, c.occupancy, smem, &occ));
   }
   if ((rc = plan(m, a, ws, st))) return rc;
   BY_CU(launch_forward(bits, a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));

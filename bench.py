@@ -53,8 +53,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="eb008a644c6ba0598eda5a6273347df0b7223a57f227abc36e4f4de96674f85c",
-                       bytes_per_record=103.10,
+TRAFFIC_CAPTURE = dict(sources_sha256="30b07860ef70ff0ddbe971328ddec86788eab887c624a06129fee1e4dff480fb",
+                       bytes_per_record=103.28,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

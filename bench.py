@@ -173,19 +173,25 @@ def barrier():
 
 
 # ------------------------------------------------------------ CPU oracle --
-def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = 1 << 22):
+CHECK_RECORDS = 1 << 22   # prefix of the main workload the oracle runs on
+
+
+def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = CHECK_RECORDS):
     """The FP64 oracle, as it stands, on this host's cores: eval at omega_o
     (with pdf) plus one sample per record, over a bounded prefix of the
-    workload, repeated until about target_s of CPU time has passed."""
+    workload, repeated until about target_s of CPU time has passed.  Also
+    returns the first pass's outputs (for the parity report)."""
     import oracle
     threads = os.cpu_count() or 1
     mats = I.materials(cfg)
     n = min(max_records, I.N_RECORDS[cfg])
     rec = I.records(cfg, 0, n)
-    done, t0 = 0, time.perf_counter()
+    done, t0, first = 0, time.perf_counter(), None
     while True:
-        oracle.eval_records(mats, rec, threads=threads)
-        oracle.sample_records(mats, rec, threads=threads)
+        ev = oracle.eval_records(mats, rec, threads=threads)
+        sa = oracle.sample_records(mats, rec, threads=threads)
+        if first is None:
+            first = (ev, sa)
         done += n
         dt = time.perf_counter() - t0
         if dt >= target_s:
@@ -193,7 +199,38 @@ def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = 1 << 22
     return dict(value=done / dt, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, eval(+pdf) and "
                        f"one sample each, FP64, {threads} threads, {done // n} passes",
-                seconds=dt, records=done)
+                seconds=dt, records=done), first
+
+
+def parity_report(gpu: dict, first) -> dict:
+    """The benchmark's own outputs against the oracle's on the same records:
+    status agreement, the share within 1e-4 relative + 1e-6 absolute (f, pdf
+    at omega_o and the sample's weight and pdf, where both report a valid
+    result), and relative-error quantiles.  The maximum includes records at
+    a branch boundary of the model (argmin ties, fiber cusps, grazing
+    directions), where either side is correct; the parity tests bracket those
+    by perturbing the inputs."""
+    (fo, po, so), (wo_o, w_o, ps_o, ss_o, lb_o) = first
+    n = so.shape[0]
+    st, ls = gpu["status"][:n], gpu["lobe_status"][:n]
+    ok = (st == 0) & (so == 0)
+    oks = ((ls & 15) == 0) & (ss_o == 0) & ((ls >> 4) == lb_o)
+
+    def rel(g, o, m):
+        e = np.abs(g - o) / (np.abs(o) + 1e-6 / 1e-4)
+        return e[..., m].reshape(-1) if e.ndim == 1 else e[:, m].max(axis=0)
+    errs = np.concatenate([np.maximum(rel(gpu["f"][:, :n], fo, ok), rel(gpu["pdf"][:n], po, ok)),
+                           np.maximum(rel(gpu["weight"][:, :n], w_o, oks),
+                                      rel(gpu["pdf_s"][:n], ps_o, oks))])
+    q = np.quantile(errs, [0.5, 0.99, 0.999]) if errs.size else [0.0] * 3
+    return dict(records=int(n), status_equal=float((st == so).mean()),
+                sample_status_equal=float((ls == (ss_o | (lb_o << 4))).mean()),
+                within_tol=float((errs <= 1e-4).mean()) if errs.size else 1.0,
+                rel_err_p50=float(q[0]), rel_err_p99=float(q[1]), rel_err_p999=float(q[2]),
+                rel_err_max=float(errs.max()) if errs.size else 0.0,
+                note="relative error |gpu - oracle| / (|oracle| + 1e-2); within_tol: share "
+                     "at most 1e-4, i.e. within 1e-4 relative + 1e-6 absolute; the max includes "
+                     "records at branch boundaries, where either side is correct")
 
 
 def run_reference(args):
@@ -445,12 +482,16 @@ def main():
                                 fused_speedup_vs_plain=ms_plain / ms_step,
                                 plain_launches_per_step=3 * len(mats))
         del ds, po, plain_out
+        # the timed steps' outputs on the records the oracle checks
+        m = min(CHECK_RECORDS, n)
+        gpu_check = {k: (v[..., :m].cpu().numpy()) for k, v in out.items()}
         del d, out
         torch.cuda.empty_cache()
 
         if not args.main_only:
             line["workloads"] = other_workloads(api, N, torch, args, sm_count)
-        line["cpu_baseline"] = cpu_oracle_rate(cfg)
+        line["cpu_baseline"], first = cpu_oracle_rate(cfg)
+        line["parity"] = parity_report(gpu_check, first)
     print(json.dumps(line), flush=True)
 
 

@@ -140,3 +140,36 @@ def test_two_rank_gradient_allreduce_gloo():
     for r in (0, 1):
         np.testing.assert_allclose(res[r], full, rtol=1e-10, atol=1e-12)
     del torch
+
+
+def test_bench_parity_report_counts_planted_errors():
+    # the bench's parity summary: a GPU result equal to the oracle's up to
+    # float32 rounding is within tolerance; planted errors of 1% (f) and a
+    # status mismatch are counted, and a record whose sampled lobe differs
+    # is left out of the sample comparison
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    n = 2000
+    g = np.random.default_rng(3)
+    fo, po = g.random((3, n)) + 0.1, g.random(n) + 0.1
+    so = np.zeros(n, np.uint8)
+    so[:20] = 1
+    w_o, ps_o = g.random((3, n)) + 0.1, g.random(n) + 0.1
+    ss_o = np.zeros(n, np.uint8)
+    lb_o = g.integers(0, 4, n).astype(np.uint8)
+    gpu = dict(f=fo.astype(np.float32), pdf=po.astype(np.float32), status=so.copy(),
+               weight=w_o.astype(np.float32), pdf_s=ps_o.astype(np.float32),
+               lobe_status=(ss_o | (lb_o << 4)).astype(np.uint8))
+    gpu["f"][1, 100] *= 1.01
+    gpu["f"][0, 101] *= 1.01
+    gpu["status"][5] = 0                       # status mismatch (and not compared)
+    gpu["lobe_status"][7] = (lb_o[7] ^ 1) << 4  # other lobe: left out
+    gpu["weight"][2, 7] *= 2.0
+    r = bench.parity_report(gpu, ((fo, po, so), (None, w_o, ps_o, ss_o, lb_o)))
+    assert r["records"] == n
+    assert r["status_equal"] == (n - 1) / n
+    assert r["sample_status_equal"] == (n - 1) / n
+    n_cmp = (n - 20) + (n - 1)                 # eval records both ok + sample records kept
+    assert abs(r["within_tol"] - (n_cmp - 2) / n_cmp) < 1e-12
+    assert 0.009 < r["rel_err_max"] < 0.011 and r["rel_err_p50"] < 1e-6

@@ -272,7 +272,9 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
       if (fmaf(-perp, perp, Rp2) >= 0.f) todo |= 1u << k;
     }
     // updates 1 .. N_it - 1; t at the entry of update N_it - n_re is where
-    // the exact re-run starts
+    // the exact re-run starts.  The update loops stay rolled: unrolled
+    // copies of these bodies cost more in instruction fetch (the kernels are
+    // large, and their warps spread over them) than they save in branches.
     const int n_mid = m.nit - n_re > 1 ? m.nit - n_re : 1;
     if constexpr (PLIES == 1) {
       while (todo) {
@@ -294,8 +296,10 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           // ply is flagged and its t no longer used
           t = fmaxf(-bb - sqrtf(disc), 0.f);
         };
+#pragma unroll 1
         for (int n = 1; n < n_mid; ++n) update();
         const float t_re = m.nit > n_re ? t : 0.f;
+#pragma unroll 1
         for (int n = n_mid; n < m.nit; ++n) update();
         consider(k, hit, t, t_re);
       }
@@ -332,8 +336,10 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
           ta = fmaxf(-ba - sqrtf(da), 0.f);
           tb = fmaxf(-bb - sqrtf(db), 0.f);
         };
+#pragma unroll 1
         for (int n = 1; n < n_mid; ++n) update();
         const float ta_re = m.nit > n_re ? ta : 0.f, tb_re = m.nit > n_re ? tb : 0.f;
+#pragma unroll 1
         for (int n = n_mid; n < m.nit; ++n) update();
         consider(ka, ha, ta, ta_re);
         if (two) consider(kb, hb, tb, tb_re);
@@ -351,6 +357,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   const S sk = s0v * m.rot_c[best] + c0v * m.rot_s[best];
   S best_t = S(t_start), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
   bool grazed = false;
+#pragma unroll 1
   for (int i = 0; i < n_upd; ++i) {
     S sd, cd;
     xsincos_turns(mv.kp * (kappa * best_t), &sd, &cd);

@@ -272,9 +272,10 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
       if (fmaf(-perp, perp, Rp2) >= 0.f) todo |= 1u << k;
     }
     // updates 1 .. N_it - 1; t at the entry of update N_it - n_re is where
-    // the exact re-run starts.  The update loops stay rolled: unrolled
-    // copies of these bodies cost more in instruction fetch (the kernels are
-    // large, and their warps spread over them) than they save in branches.
+    // the exact re-run starts.  The update loops (like the node and
+    // shadowing loops) stay rolled: unrolled copies of these bodies cost more
+    // in instruction fetch (the kernels are large, and their warps spread
+    // over them) than they save in branches.
     const int n_mid = m.nit - n_re > 1 ? m.nit - n_re : 1;
     if constexpr (PLIES == 1) {
       while (todo) {
@@ -422,6 +423,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   // Sec. 4.1.4: ply shadowing by the in-plane chords through the other
   // plies of this cross-section; fiber shadowing from the map
   S occ = S(0.f);
+#pragma unroll 1
   for (int j = 1; j < m.np; ++j) {
     int r = j;
     const float rc = m.rot_c[r], rs = m.rot_s[r];
@@ -496,6 +498,7 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   const bool near = fp.K == 1 && fp.width == 0.0f;
   const bool jitter = sc != nullptr && (sc->flags & STOCH_JITTER_NODES) != 0;
   U64x4 rnd = {{0, 0, 0, 0}};
+#pragma unroll 1
   for (int j = 0; j < fp.K; ++j) {
     float X0x, X0y;
     if (near) {

@@ -267,13 +267,14 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     // sin/cos): a ply whose circle the ray misses there is not hit whatever
     // the later updates give, so only the plies that pass it are iterated.
     uint32_t todo = 0;
+#pragma unroll 1
     for (int k = 0; k < m.np; ++k) {
       const float perp = px0 - (B0 * m.rot_c[k] - A0 * m.rot_s[k]);
       if (fmaf(-perp, perp, Rp2) >= 0.f) todo |= 1u << k;
     }
     // updates 1 .. N_it - 1; t at the entry of update N_it - n_re is where
-    // the exact re-run starts.  The update loops (like the node and
-    // shadowing loops) stay rolled: unrolled copies of these bodies cost more
+    // the exact re-run starts.  The update loops (like the update-0 mask,
+    // node and shadowing loops) stay rolled: unrolled copies of these bodies cost more
     // in instruction fetch (the kernels are large, and their warps spread
     // over them) than they save in branches.
     const int n_mid = m.nit - n_re > 1 ? m.nit - n_re : 1;

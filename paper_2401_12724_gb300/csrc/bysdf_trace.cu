@@ -47,6 +47,8 @@ __device__ __forceinline__ float line_offset(const PieceS& p, float bx, float by
 }
 
 constexpr int kGroupPieces = 8;
+// the piece rounds give each of four groups 8 lanes (lane >> 3, lane & 7)
+static_assert(kGroupPieces == 8, "the piece rounds assume groups of 8 pieces");
 
 // The line of a ray with origin o_i and unit direction u_i lies at least
 // dist(C, axis) - ro - (|C - oc| + ro) * del from a point C, where the axis

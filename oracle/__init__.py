@@ -26,9 +26,13 @@ from .oracle import (  # noqa: F401
     ggx_g1,
     grad_ext_records,
     grad_records,
+    internal_offsets,
     layout,
     lib,
     lobes,
+    margin,
+    margins,
+    MARGIN_CLASSES,
     migration_info,
     migration_texels,
     btdf,

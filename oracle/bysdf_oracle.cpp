@@ -134,6 +134,36 @@ inline Cnt log(Cnt a) { return cnt(4, std::log(a.v)); }
 inline Cnt asin(Cnt a) { return cnt(4, std::asin(a.v)); }
 inline Cnt atan2(Cnt y, Cnt x) { return cnt(4, std::atan2(y.v, x.v)); }
 
+// Discontinuity margins (for the parity tests): at each branch point of the
+// model -- and at the steep spots where a result changes faster than rounding
+// can be controlled -- the evaluation notes how far the deciding quantity is
+// from its threshold, in the quantity's own units (lengths in yarn radii,
+// cosines, fiber periods, probabilities).  A record's margin in class k is the
+// smallest distance noted in that class.  Only evaluations with a margin
+// buffer set (orc_margins) note anything.
+enum {
+  MG_GRAZE = 0,   // ply trace: ray vs ply circle tangent, every update (Sec. 3.4)
+  MG_GAP,         // closest ply: gap to the next hit ply's distance (Sec. 3.4)
+  MG_CUSP,        // fiber maps: distance to the cusp texel interval (Sec. 3.5.1)
+  MG_AXIS,        // in-plane length of omega_i (rays along the yarn axis)
+  MG_HEMI,        // hemisphere side of omega_i / omega_o at the shading normal
+  MG_EXIT,        // transmission: entry / exit sides, total internal reflection (Sec. 4.1.2)
+  MG_LOBE,        // lobe choice by u0 (Sec. 4.1.5)
+  MG_SAMPLE,      // validity of the sampled direction, sampler frame
+  MG_SHADOW,      // ply shadowing: shadow ray vs another ply's circle (Sec. 4.1.4)
+  MG_N = 10
+};
+thread_local double* g_mg = nullptr;
+inline void mg(int k, double dist) {
+  if (g_mg) g_mg[k] = std::min(g_mg[k], std::fabs(dist));
+}
+// Offsets of two internal quantities (for the parity tests' conditioning
+// measure, which asks how far the result moves when they carry the rounding
+// of a float32 evaluation): the in-plane hit distance t of every node and
+// the ply azimuth u_ply that sets the fiber phase.  Zero except between
+// orc_set_internal_offsets calls; process-wide, set between evaluations.
+double g_off_t = 0.0, g_off_uply = 0.0;
+
 inline double val(double x) { return x; }
 template <int N> double val(const Dual<N>& x) { return x.v; }
 inline double val(const Cnt& x) { return x.v; }
@@ -160,6 +190,10 @@ template <class S> V3<S> cross(const V3<S>& a, const V3<S>& b) {
 template <class S> S norm(const V3<S>& a) { using std::sqrt; return sqrt(dot(a, a)); }
 template <class S> V3<S> normalize(const V3<S>& a) { return a * (S(1.0) / norm(a)); }
 template <class S> V3<S> lift(const double* p) { return {S(p[0]), S(p[1]), S(p[2])}; }
+// dot product of the values (margin notes: not part of the counted work)
+template <class S> double dotv(const V3<S>& a, const V3<S>& b) {
+  return val(a.x) * val(b.x) + val(a.y) * val(b.y) + val(a.z) * val(b.z);
+}
 
 // ---------------------------------------------------------------- material --
 // Ply and fiber layout.  The paper gives no layout (Sec. 3.4, 3.5); reading:
@@ -488,6 +522,13 @@ void fiber_lookup_tab(const MatStatic& st, int Mk, const std::vector<double>& ta
   const S a = w + 0.5 - std::floor(val(w + 0.5));
   const S tau = a * (double)T - 0.5;
   const double fl = std::floor(val(tau));
+  // margin: the interval between the last and the first texel centre holds
+  // the cusp, where delta jumps across the whole fiber; distance to it in
+  // fiber periods (0 inside)
+  {
+    const double tv = val(tau);
+    mg(MG_CUSP, (tv < 0.0 || tv >= T - 1.0) ? 0.0 : std::min(tv, (T - 1.0) - tv) / T);
+  }
   const S f = tau - fl;
   const int i0 = (((int)fl) % T + T) % T;
   const int i1 = (i0 + 1) % T;
@@ -520,6 +561,10 @@ S ply_occlusion(const Mat<S>& m, int k, const S& psi_k, const S& xx, const S& xy
     const S b = qx * wx + qy * wy;
     const S cc = qx * qx + qy * qy - L.Rp * L.Rp;
     const S disc = b * b - cc;
+    // margin: the shadow ray grazing ply j's circle ahead of x (the chord
+    // length has an infinite slope there)
+    if (val(-b) + L.Rp > 0.0)
+      mg(MG_SHADOW, L.Rp - std::sqrt(std::max(L.Rp * L.Rp - val(disc), 0.0)));
     if (disc > 0.0) {
       const S sq = sqrt(disc);
       const S s1 = -b - sq, s2 = -b + sq;
@@ -608,6 +653,9 @@ Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
       const S b = qx * ex + qy * ey;
       const S cc = qx * qx + qy * qy - L.Rp * L.Rp;
       const S disc = b * b - cc;
+      // margin: distance of the in-plane ray from the ply circle's edge,
+      // R_p - |perp| with perp^2 = R_p^2 - disc
+      mg(MG_GRAZE, L.Rp - std::sqrt(std::max(L.Rp * L.Rp - val(disc), 0.0)));
       if (disc < 0.0) {
         hit = false;
         break;
@@ -628,10 +676,14 @@ Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
     }
   }
   if (best < 0) return g;  // Sec. 3.4: no ply hit, the ray passes through.
+  // margin: the closest ply changes where another hit ply is as near
+  for (int k = 0; k < Np; ++k)
+    if (k != best && g.t_ply[k] >= 0.0) mg(MG_GAP, g.t_ply[k] - val(best_t));
   g.hit = true;
   g.k = best;
   // Sec. 3.4: hit point, ply normal (away from the ply centre in the circular
   // cross-section) and ply tangent (derivative of the helix through x).
+  if (g_off_t != 0.0) best_t = best_t + g_off_t;
   const S xx = X0x + best_t * ex, xy = X0y + best_t * ey;
   const S zx = v + kappa * best_t;
   g.x = mk<S>(xx, xy, zx);
@@ -646,6 +698,7 @@ Node<S> node_geometry(const Mat<S>& m, double X0x, double X0y, double ex,
   // from the ply centre's radial direction; fiber phase and 1D maps.
   const S ecx = cos(best_psi), ecy = sin(best_psi);
   g.u_ply = atan2(ecx * g.np.y - ecy * g.np.x, ecx * g.np.x + ecy * g.np.y);
+  if (g_off_uply != 0.0) g.u_ply = g.u_ply + g_off_uply;
   const S theta_f = g.u_ply - m.omega_f * zx;
   if (st.d.migration_maps > 1)
     migration_lookup(m, g.u_ply, zx, &g.delta, &g.of);
@@ -714,6 +767,7 @@ Geo<S> geometry(const Mat<S>& m, const Rec& q, const V3<S>& wi, const Stoch* sc 
   const double g0 = std::asin(q.h);
   const double ex = -std::cos(q.u - g0), ey = -std::sin(q.u - g0);
   const S Lxy = sqrt(wi.x * wi.x + wi.y * wi.y);
+  mg(MG_AXIS, val(Lxy));
   if (val(Lxy) < 1e-7) return G;
   const S kappa = -wi.z / Lxy;
   V3<S> ns = mk<S>(S(0.0), S(0.0), S(0.0)), ts = ns, xs = ns;
@@ -793,6 +847,7 @@ V3<S> vndf_sample(const V3<S>& w, const S& at, const S& ab, double u0, double u1
   const V3<S> V = normalize(mk<S>(at * w.x, ab * w.y, w.z));
   const S lensq = V.x * V.x + V.y * V.y;
   V3<S> T1 = mk<S>(S(1.0), S(0.0), S(0.0));
+  mg(MG_SAMPLE, std::sqrt(val(lensq)));  // margin: the disk frame turns with V
   if (lensq > 0.0) {
     const S il = 1.0 / sqrt(lensq);
     T1 = mk<S>(-V.y * il, V.x * il, S(0.0));
@@ -851,6 +906,7 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi,
     s.b = -s.b;
   }
   s.mui = dot(s.wi, s.n);
+  mg(MG_HEMI, val(s.mui));  // margin: the side of omega_i decides the flip
   // Sec. 4.2: beta_multi = beta + (h2 - h1) / 2 (reading of the normaliser);
   // GGX alpha = beta in radians, clamped to [1e-3, 1.5].
   const double half_w = 0.5 * (double)G.fp.width;
@@ -881,13 +937,17 @@ Shade<S> make_shade(const Mat<S>& m, const Geo<S>& G, const V3<S>& wi,
     const V3<S> ml = vndf_sample(to_local(s.wi, s.t, s.b, s.n), s.at, s.ab, v0, v1);
     mn = s.t * ml.x + s.b * ml.y + s.n * ml.z;
     ci = dot(s.wi, mn);
+    mg(MG_EXIT, val(ci));
   }
   const S s2t = (1.0 - ci * ci) / (d.eta * d.eta);
+  mg(MG_EXIT, std::sqrt(std::fabs(1.0 - val(s2t))));  // refraction edge, as a cosine
   if (!(s.mui > 0.0) || !(ci > 0.0) || s2t >= 1.0) return s;
   const S cost = sqrt(1.0 - s2t);
   const V3<S> din = s.wi * (-1.0 / d.eta) + mn * (ci / d.eta - cost);
+  mg(MG_EXIT, dotv(din, s.n));
   if (!(dot(din, s.n) < 0.0)) return s;
   const S a = din.x * din.x + din.y * din.y;
+  mg(MG_EXIT, std::sqrt(val(a)));
   if (!(a > 1e-12)) return s;
   const S bq = G.x.x * din.x + G.x.y * din.y;
   const S c = G.x.x * G.x.x + G.x.y * G.x.y - d.yarn_radius * d.yarn_radius;
@@ -927,6 +987,7 @@ Lobes<S> eval_lobes(const Shade<S>& s, const V3<S>& wo) {
   for (int c = 0; c < 3; ++c) L.fxb[c] = L.fyb[c] = S(0.0);
   const S muo = dot(wo, s.n);
   if (!(s.mui > 0.0)) return L;
+  mg(MG_HEMI, val(muo));  // margin: the side of omega_o picks the lobes
   if (muo > 0.0) {
     // Eq. 2, first case (reflection, Walter et al. 2007 with GGX).
     const V3<S> h = normalize(s.wi + wo);
@@ -955,10 +1016,18 @@ Lobes<S> eval_lobes(const Shade<S>& s, const V3<S>& wo) {
     // exit point y from inside (eta) to outside (1), times tau^{N_i}.
     if (s.tt_ok) {
       const S ion = dot(s.iy, s.ny), oon = dot(wo, s.ny);
+      mg(MG_EXIT, val(ion));
+      mg(MG_EXIT, val(oon));
       if (ion < 0.0 && oon > 0.0) {
         V3<S> ht = normalize(-(s.iy * s.eta + wo));
+        mg(MG_EXIT, dotv(ht, s.ny));
         if (dot(ht, s.ny) < 0.0) ht = -ht;
         const S ih = dot(s.iy, ht), oh = dot(wo, ht);
+        mg(MG_EXIT, val(ih));
+        mg(MG_EXIT, val(oh));
+        // margin: total internal reflection at y (F_y = 1 beyond it), as the
+        // refraction edge, as a cosine
+        mg(MG_EXIT, std::sqrt(std::fabs(1.0 - (1.0 - val(ih) * val(ih)) * s.eta * s.eta)));
         if (ih < 0.0 && oh > 0.0) {
           const S den = s.eta * ih + oh;
           const V3<S> hl = to_local(ht, s.ty, s.by, s.ny);
@@ -1050,6 +1119,10 @@ Out<S> sample_one(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
   lobe_probs(s, P);
   // Sec. 4.1.5: one random number picks the lobe and is rescaled for reuse.
   double u0 = q.u0;
+  {
+    double cum = 0.0;  // margin: u0 at a boundary of the lobe choice
+    for (int k = 0; k < 3; ++k) mg(MG_LOBE, u0 - (cum += P[k]));
+  }
   int lobe = 3;
   double lo = 0.0;
   for (int k = 0; k < 3; ++k) {
@@ -1070,6 +1143,7 @@ Out<S> sample_one(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
     const V3<S> ml = vndf_sample(il, s.at, s.ab, ur, q.u1);
     const V3<S> mw = s.t * ml.x + s.b * ml.y + s.n * ml.z;
     wo = mw * (2.0 * dot(s.wi, mw)) - s.wi;
+    mg(MG_SAMPLE, dotv(wo, s.n));
     ok = dot(wo, s.n) > 0.0;
   } else if (lobe == 1) {
     // GGX visible-normal sample at y about the inner normal, refraction out.
@@ -1081,10 +1155,14 @@ Out<S> sample_one(const Mat<S>& m, const Rec& q, const Stoch* sc = nullptr) {
       const V3<S> mw = Tn * ml.x + Bn * ml.y + Nn * ml.z;
       const S c = dot(s.iy, mw);
       const S s2t = s.eta * s.eta * (1.0 - c * c);
+      mg(MG_SAMPLE, val(c));
+      mg(MG_SAMPLE, std::sqrt(std::fabs(1.0 - val(s2t))));
       if (!(c > 0.0) || s2t >= 1.0) {
         ok = false;
       } else {
         wo = normalize(s.iy * (-s.eta) + mw * (s.eta * c - sqrt(1.0 - s2t)));
+        mg(MG_SAMPLE, dotv(wo, s.ny));
+        mg(MG_SAMPLE, dotv(wo, s.n));
         ok = dot(wo, s.ny) > 0.0 && dot(wo, s.n) < 0.0;
       }
     }
@@ -1338,6 +1416,42 @@ int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r
     }
   });
   return 0;
+}
+
+int orc_margins(const orc_material* m, int n_mat, const orc_records* r, int64_t n, int op,
+                uint64_t seed, int64_t index_offset, uint32_t flags, double* out,
+                int n_threads) {
+  static_assert(MG_N == ORC_MG_N, "margin classes");
+  Batch B = make_batch(m, n_mat);
+  if (!B.ok || op < 0 || op > 1) return -1;
+  parallel_for(n, n_threads, [&](int64_t b, int64_t e, int) {
+    std::vector<Mat<double>> mats;
+    for (auto& st : B.st) mats.push_back(make_mat<double>(st, false));
+    Stoch sc;
+    sc.jitter = (flags & ORC_STOCH_JITTER_NODES) != 0;
+    sc.rough = (flags & ORC_STOCH_ROUGH_ENTRY) != 0;
+    sc.seed = seed;
+    for (int64_t i = b; i < e; ++i) {
+      double* row = out + i * MG_N;
+      for (int k = 0; k < MG_N; ++k) row[k] = HUGE_VAL;
+      const Rec q = read_rec(r, i, n);
+      sc.index = (uint64_t)(index_offset + i);
+      const Stoch* scp = flags ? &sc : nullptr;
+      if (!valid_rec(q, n_mat, op == 0, op == 1)) continue;
+      g_mg = row;
+      if (op == 0)
+        eval_one(mats[q.mat], q, scp);
+      else
+        sample_one(mats[q.mat], q, scp);
+      g_mg = nullptr;
+    }
+  });
+  return 0;
+}
+
+void orc_set_internal_offsets(double dt, double du_ply) {
+  g_off_t = dt;
+  g_off_uply = du_ply;
 }
 
 int orc_stoch_nodes(double h0, int has_ratio, double ratio, int k_max, uint64_t seed,

@@ -127,6 +127,33 @@ int orc_eval_stochastic(const orc_material* m, int n_mat, const orc_records* r, 
 int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r, int64_t n,
                           uint64_t seed, int64_t index_offset, uint32_t flags, double* wo,
                           double* weight, double* pdf, uint8_t* lobe_status, int n_threads);
+/* Discontinuity margins (parity tests).  For each record, the evaluation of
+ * op 0 (eval and pdf at omega_o) or op 1 (one sample from u0, u1) -- with the
+ * stochastic estimators when flags != 0 -- notes at every branch point of the
+ * model, and at the steep spots where the result moves faster than float32
+ * rounding can be followed, how far the deciding quantity is from its
+ * threshold, in that quantity's own units:
+ *   0 ply trace: R_p - |perp| of the in-plane ray at every update (hit/miss)
+ *   1 closest ply: distance gap to the next hit ply
+ *   2 fiber maps: distance in fiber periods to the cusp texel interval
+ *   3 in-plane length of omega_i (rays along the yarn axis)
+ *   4 omega_i . n and omega_o . n at the shading normal (hemisphere side)
+ *   5 transmission: entry and exit side tests, total internal reflection at y
+ *   6 lobe choice: u0 against the cumulative lobe probabilities
+ *   7 sampled direction: side tests, the sampler's disk frame
+ *   8 ply shadowing: the shadow ray grazing another ply's circle
+ * out: [n][ORC_MG_N], the smallest distance per class (+inf where a record
+ * never reaches the class; the row stays +inf for invalid records). */
+#define ORC_MG_N 10
+int orc_margins(const orc_material* m, int n_mat, const orc_records* r, int64_t n, int op,
+                uint64_t seed, int64_t index_offset, uint32_t flags, double* out,
+                int n_threads);
+/* Test hook of the parity tests' conditioning measure: add dt to the in-plane
+ * hit distance of every footprint node and du_ply (radians) to its ply
+ * azimuth (and so to the fiber phase), as a float32 evaluation's rounding of
+ * these two quantities would.  Process-wide; set it between evaluations and
+ * back to (0, 0) afterwards. */
+void orc_set_internal_offsets(double dt, double du_ply);
 /* The jittered node positions h_j of one record (returns K; h_out[K]). */
 int orc_stoch_nodes(double h0, int has_ratio, double ratio, int k_max, uint64_t seed,
                     uint64_t index, double* h_out);

@@ -132,6 +132,10 @@ def lib():
         L.orc_stoch_nodes.argtypes = [C.c_double, C.c_int, C.c_double, C.c_int, C.c_uint64,
                                       C.c_uint64, P]
         L.orc_philox4x64.argtypes = [P, P, P]
+        L.orc_set_internal_offsets.argtypes = [C.c_double, C.c_double]
+        L.orc_set_internal_offsets.restype = None
+        L.orc_margins.argtypes = [MP, C.c_int, RP, C.c_int64, C.c_int, C.c_uint64, C.c_int64,
+                                  C.c_uint32, P, C.c_int]
         L.orc_trace_yarns.argtypes = [P, C.c_int, C.POINTER(RayPlanes), C.c_int64, P, P, P, P,
                                       P, P, P, P, P, P, C.c_int]
         L.orc_migration_info.argtypes = [MP, C.c_int, C.c_int64, P]
@@ -322,6 +326,51 @@ def sample_stochastic_records(mats, rec, seed: int, flags: int, index_offset: in
                                    ls.ctypes.data, threads):
         raise ValueError("oracle: bad material description")
     return wo, w, pdf, ls & 15, ls >> 4
+
+
+MG_N = 10
+MARGIN_CLASSES = ("graze", "gap", "cusp", "axis", "hemi", "exit", "lobe", "sample", "shadow")
+
+
+def margins(mats, rec, op: str = "eval", seed: int = 0, flags: int = 0, index_offset: int = 0,
+            threads: int = 1) -> np.ndarray:
+    """Discontinuity margins of each record (bysdf_oracle.h, orc_margins):
+    [ORC_MG_N, n], the smallest distance of a deciding quantity from its
+    branch threshold per class (MARGIN_CLASSES order; +inf where a record
+    never reaches the class).  op: "eval" (f and pdf at omega_o) or "sample"
+    (one sample from u0, u1); flags != 0 follows the stochastic estimators."""
+    keep = []
+    M = _materials(mats)
+    rec = dict(rec)
+    if op == "sample":
+        rec.pop("wo", None)
+    r, n = _records(rec, keep)
+    out = np.zeros((n, MG_N))
+    if lib().orc_margins(M, len(mats), C.byref(r), n, 0 if op == "eval" else 1, seed,
+                         index_offset, flags, out.ctypes.data, threads):
+        raise ValueError("oracle: bad material description")
+    return np.ascontiguousarray(out.T)
+
+
+class internal_offsets:
+    """Context manager: evaluations inside it see the in-plane hit distance
+    moved by dt and the ply azimuth by du_ply radians (orc_set_internal_offsets)."""
+
+    def __init__(self, dt: float = 0.0, du_ply: float = 0.0):
+        self.dt, self.du = dt, du_ply
+
+    def __enter__(self):
+        lib().orc_set_internal_offsets(self.dt, self.du)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_internal_offsets(0.0, 0.0)
+        return False
+
+
+def margin(mats, rec, op: str = "eval", **kw) -> np.ndarray:
+    """The smallest margin over all classes, per record."""
+    return margins(mats, rec, op, **kw).min(axis=0)
 
 
 def stoch_nodes(h0, ratio, k_max, seed, index):

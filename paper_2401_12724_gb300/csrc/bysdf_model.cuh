@@ -17,7 +17,8 @@
 
 namespace bysdf {
 
-enum { ST_OK = 0, ST_NO_HIT = 1, ST_INVALID = 2, ST_BAD_SAMPLE = 3 };
+// ST_ABORTED: not evaluated, a device-side wait gave up (see the error word)
+enum { ST_OK = 0, ST_NO_HIT = 1, ST_INVALID = 2, ST_BAD_SAMPLE = 3, ST_ABORTED = 4 };
 
 struct Record {
   float h, u, v, ratio;
@@ -568,14 +569,18 @@ __device__ __forceinline__ void geometry(const MatDev& m, const float2* map,
 
 // ------------------------------------------------------------ microfacet --
 // Unpolarised dielectric Fresnel reflectance, eta = eta_t / eta_i, cos >= 0.
+// fresnel_ct takes the cosine of the transmitted direction as well.
+template <class S>
+__device__ __forceinline__ S fresnel_ct(const S& ci, const S& ct, float eta) {
+  const S rs = (ci - eta * ct) / (ci + eta * ct);
+  const S rp = (eta * ci - ct) / (eta * ci + ct);
+  return 0.5f * (rs * rs + rp * rp);
+}
 template <class S>
 __device__ __forceinline__ S fresnel(const S& ci, float eta) {
   const S s2t = (1.0f - ci * ci) * (1.0f / (eta * eta));
   if (!(vf(s2t) < 1.0f)) return S(1.f);
-  const S ct = xsqrt(1.0f - s2t);
-  const S rs = (ci - eta * ct) / (ci + eta * ct);
-  const S rp = (eta * ci - ct) / (eta * ci + ct);
-  return 0.5f * (rs * rs + rp * rp);
+  return fresnel_ct(ci, xsqrt(1.0f - s2t), eta);
 }
 // Anisotropic GGX (Heitz 2014) in a local frame (x = t, y = b, z = n).
 template <class S>
@@ -591,6 +596,17 @@ __device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, const S& at, co
   const S an = vf(w.z) < 0.f ? -w.z : w.z;
   const S ax = at * w.x, ay = ab * w.y;
   return 2.0f * an / (an + xsqrt(an * an + ax * ax + ay * ay));
+}
+// G1(w) / |w.z| in closed form: the lobes divide G1 of the incoming
+// direction by its own cosine, which near grazing is a ratio of two small
+// numbers rounded apart; the quotient is formed without them
+template <class S>
+__device__ __forceinline__ S ggx_g1_over_cos(const V3<S>& w, const S& wm, const S& at,
+                                             const S& ab) {
+  if (!(vf(wm) * vf(w.z) > 0.f)) return S(0.f);
+  const S an = vf(w.z) < 0.f ? -w.z : w.z;
+  const S ax = at * w.x, ay = ab * w.y;
+  return 2.0f / (an + xsqrt(an * an + ax * ax + ay * ay));
 }
 // GGX visible-normal sample (Heitz 2018), local frame, w.z > 0; the disk
 // point is (r cos phi, r sin phi) with r = sqrt(u0), phi = 2 pi u1.
@@ -802,7 +818,7 @@ __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, c
   const V3<S> hl = to_local(h, ft, fb, fn), il = to_local(vi, ft, fb, fn),
               ol = to_local(wo, ft, fb, fn);
   const S D = ggx_d(hl, s.at, s.ab);
-  const S g1i = ggx_g1(il, ih, s.at, s.ab);
+  const S g1i_c = ggx_g1_over_cos(il, ih, s.at, s.ab);  // G1(i) / |i.n|
   const S g1o = ggx_g1(ol, oh, s.at, s.ab);
   if (dln_alpha) {
     // the specular value is a product with D, G1(i), G1(o): its log
@@ -815,14 +831,26 @@ __device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, c
     dln_alpha[0] = a0 + b0 + c0;
     dln_alpha[1] = a1 + b1 + c1;
   }
-  const S F = fresnel(refl ? ih : -ih, refl ? m.eta : m.inv_eta);
+  // at the exit the generalised half vector of two unit vectors gives
+  // eta^2 (1 - (i.h)^2) = 1 - (o.h)^2 exactly, so the float path takes o.h as
+  // the transmitted cosine (no cancellation next to total internal
+  // reflection); dual numbers keep the general form, whose partial
+  // derivatives in omega_o's components also hold off the unit sphere
+  S F;
   if (refl) {
-    const S q = g1i * D / (4.0f * s.mui);
+    F = fresnel(ih, m.eta);
+  } else if constexpr (is_dual<S>::value) {
+    F = fresnel(-ih, m.inv_eta);
+  } else {
+    F = fresnel_ct(-ih, oh, m.inv_eta);
+  }
+  if (refl) {
+    const S q = g1i_c * D * 0.25f;
     L.spec_u = F * g1o * q;
     L.pR = q;
   } else {
     const S den = m.eta * ih + oh;
-    const S q = g1i * (-ih) * D * oh / ((-ion) * den * den);
+    const S q = g1i_c * (-ih) * D * oh / (den * den);
     L.spec_u = s.tx * s.tau * (1.0f - F) * g1o * q;
     L.pT = q;
   }

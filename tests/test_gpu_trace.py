@@ -104,10 +104,10 @@ def test_traced_records_feed_the_bysdf(api, orc):
     f, p, st = np_(out["f"]), np_(out["pdf"]), np_(out["status"])
     assert np.all(st[g["mat_id"] < 0] == 2)
     fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, rec)
-    PU.assert_status(st, sb, [q[2] for q in pert], "trace.status")
-    PU.assert_parity(f, fb, [q[0] for q in pert], "trace.f")
-    PU.assert_parity(p, pb, [q[1] for q in pert], "trace.pdf")
+    view = PU.oracle_view(orc, fn, mats, rec)
+    PU.assert_status(st, view, "trace.status")
+    PU.assert_parity(f, view, 0, "trace.f", gpu_status=st)
+    PU.assert_parity(p, view, 1, "trace.pdf", gpu_status=st)
     assert (st == 0).mean() > 0.5
 
 

@@ -39,14 +39,16 @@ UNIT = "records/s"
 MAIN_CFG = 2
 
 # Algorithmic work per record, counted by the FP64 oracle's operation-counting
-# scalar on 4096 records of each workload (oracle/count_ops.py): FP32 flops
-# (adds + multiplies) and XU ops (divisions, square roots, transcendentals).
+# scalar on 4096 records of each workload (oracle/count_ops.py, which also
+# gives the backward's count: one recompute plus one reverse sweep): FP32
+# flops (adds + multiplies) and XU ops (divisions, square roots,
+# transcendentals).  tests/test_op_counts.py recounts and compares.
 OPS = {
-    1: dict(eval=(476.2, 67.9)),
-    2: dict(eval=(515.3, 73.6), fused=(695.9, 92.6)),
-    3: dict(eval=(2941.7, 458.5), fused=(3128.3, 478.0)),
-    4: dict(eval=(557.1, 79.7), fused=(744.2, 99.3)),
-    5: dict(eval=(412.0, 58.6)),
+    1: dict(eval=(480.3, 67.9)),
+    2: dict(eval=(519.5, 73.6), fused=(700.1, 92.6)),
+    3: dict(eval=(2946.4, 458.5), fused=(3133.1, 478.0)),
+    4: dict(eval=(561.6, 79.7), fused=(748.7, 99.3)),
+    5: dict(eval=(415.9, 58.6), backward=(1862.6, 117.2)),
 }
 # DRAM traffic of the fused kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch on the first 2^22 records of the
@@ -174,6 +176,7 @@ def barrier():
 
 # ------------------------------------------------------------ CPU oracle --
 CHECK_RECORDS = 1 << 22   # prefix of the main workload the oracle runs on
+RULE_RECORDS = 1 << 18    # prefix the tests' parity rule is applied to
 
 
 def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = CHECK_RECORDS):
@@ -200,6 +203,57 @@ def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = CHECK_R
                 sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, eval(+pdf) and "
                        f"one sample each, FP64, {threads} threads, {done // n} passes",
                 seconds=dt, records=done), first
+
+
+def parity_rule(gpu: dict, cfg: int) -> dict:
+    """The parity tests' rule (oracle/parity.py) on the first RULE_RECORDS
+    records of the timed outputs: strict on every record the oracle finds
+    well-conditioned (margin to every branch point >= 1e-4, first-order
+    change under one float32 rounding of its inputs <= a quarter of the
+    tolerance), the oracle's bracket on the others."""
+    import oracle
+    from oracle import parity as PU
+    threads = os.cpu_count() or 1
+    mats = I.materials(cfg)
+    m = min(RULE_RECORDS, gpu["status"].shape[0])
+    rec = I.records(cfg, 0, m)
+    out = dict(records=m)
+    try:
+        view = PU.oracle_view(oracle, lambda r: oracle.eval_records(mats, r, threads=threads),
+                              mats, rec)
+        st = gpu["status"][:m]
+        PU.assert_status(st, view, "bench.status")
+        r_f = PU.assert_parity(gpu["f"][:, :m], view, 0, "bench.f", gpu_status=st)
+        r_p = PU.assert_parity(gpu["pdf"][:m], view, 1, "bench.pdf", gpu_status=st)
+
+        def code(r):
+            wo, w, p, s, lb = oracle.sample_records(mats, r, threads=threads)
+            return wo, w, p, s | (lb << 4)
+        sv = PU.oracle_view(oracle, code, mats, rec, sample=True, values=(1, 2), status_idx=3,
+                            angle_idx=0)
+        ls = gpu["lobe_status"][:m]
+        PU.assert_status(ls, sv, "bench.lobe_status")
+        both = ((sv.base[3] & 15) == 0) & ((ls & 15) == 0)
+        with np.errstate(invalid="ignore"):
+            ang = np.where(both, PU.angle_between(gpu["wo"][:, :m], sv.base[0]), 0.0)
+        r_wo = PU.assert_parity(gpu["wo"][:, :m], sv, 0, "bench.wo", err=ang / PU.ANGLE,
+                                gpu_status=ls, direction=True)
+        r_w = PU.assert_parity(gpu["weight"][:, :m], sv, 1, "bench.weight", gpu_status=ls)
+        r_ps = PU.assert_parity(gpu["pdf_s"][:m], sv, 2, "bench.pdf_s", gpu_status=ls)
+        out.update(passed=True, within_tol_well_conditioned=1.0,
+                   eval=dict(strict_f=r_f["strict"], strict_pdf=r_p["strict"],
+                             well_conditioned=r_f["well_conditioned"],
+                             low_margin=r_f["low_margin"], ill_conditioned=r_f["ill_conditioned"],
+                             undetermined=r_f["undetermined"]),
+                   sample=dict(strict_wo=r_wo["strict"], strict_weight=r_w["strict"],
+                               strict_pdf=r_ps["strict"],
+                               well_conditioned=r_w["well_conditioned"],
+                               low_margin=r_w["low_margin"],
+                               ill_conditioned=r_w["ill_conditioned"],
+                               undetermined=r_w["undetermined"]))
+    except AssertionError as e:
+        out.update(passed=False, failure=str(e)[:400])
+    return out
 
 
 def parity_report(gpu: dict, first) -> dict:
@@ -472,15 +526,20 @@ def main():
             api.plain(N.OP_SAMPLE, M, ds, seg, out=plain_out)
             api.plain(N.OP_PDF, M, ds, seg, out=plain_out)
         ms_plain, _ = timed(plain_step, max(3, args.steps // 2), 2)
+        # like for like: the fused op in the plain per-material form
+        ms_plain_fused, _ = timed(lambda: api.plain_fused(M, ds, seg, out=po),
+                                  max(3, args.steps // 2), 2)
         # the same three ops as separate persistent calls (no fusion)
         sep = lambda: (api.eval(M, d, out=out), api.sample(M, d, out=dict(  # noqa: E731
             wo=out["wo"], weight=out["weight"], pdf=out["pdf_s"], lobe_status=out["lobe_status"])),
             api.pdf(M, d, out=out))
         ms_sep, _ = timed(sep, max(3, args.steps // 2), 2)
-        line["vs_plain"] = dict(plain_records_per_s=n / (ms_plain / 1e3),
+        line["vs_plain"] = dict(plain_fused_records_per_s=n / (ms_plain_fused / 1e3),
+                                fused_speedup_vs_plain_fused=ms_plain_fused / ms_step,
+                                plain_fused_launches_per_step=len(mats),
+                                plain_three_ops_records_per_s=n / (ms_plain / 1e3),
                                 separate_persistent_records_per_s=n / (ms_sep / 1e3),
-                                fused_speedup_vs_plain=ms_plain / ms_step,
-                                plain_launches_per_step=3 * len(mats))
+                                fused_speedup_vs_plain_three_ops=ms_plain / ms_step)
         del ds, po, plain_out
         # the timed steps' outputs on the records the oracle checks
         m = min(CHECK_RECORDS, n)
@@ -492,6 +551,7 @@ def main():
             line["workloads"] = other_workloads(api, N, torch, args, sm_count)
         line["cpu_baseline"], first = cpu_oracle_rate(cfg)
         line["parity"] = parity_report(gpu_check, first)
+        line["parity"]["rule"] = parity_rule(gpu_check, cfg)
     print(json.dumps(line), flush=True)
 
 
@@ -609,18 +669,16 @@ def other_workloads(api, N, torch, args, sm_count):
     with torch.cuda.graph(g):
         api.eval_sample_pdf(M, d, out=o)
     ms_graph, _ = timed(g.replay, steps, 2)
-    po = dict(f=o["f"], wo=o["wo"], weight=o["weight"], pdf=o["pdf"], status=o["status"])
 
-    def plain_step():
-        api.plain(N.OP_EVAL, M, d, seg, out=po)
-        api.plain(N.OP_SAMPLE, M, d, seg, out=po)
-        api.plain(N.OP_PDF, M, d, seg, out=po)
-    ms_plain, _ = timed(plain_step, max(2, steps // 2), 1)
+    ms_plain, _ = timed(lambda: api.plain_fused(M, d, seg, out=o), max(2, steps // 2), 1)
+    # the persistent fused kernel without the graph (one launch per call)
+    ms_nograph, _ = timed(lambda: api.eval_sample_pdf(M, d, out=o), max(2, steps // 2), 1)
     res[I.WORKLOAD_NAME[4]] = dict(records_per_s=n / (ms_graph / 1e3), ms=ms_graph, records=n,
-                                   autotuned=tuned, plain_records_per_s=n / (ms_plain / 1e3),
-                                   speedup_vs_plain=ms_plain / ms_graph,
+                                   autotuned=tuned, plain_fused_records_per_s=n / (ms_plain / 1e3),
+                                   speedup_vs_plain_fused=ms_plain / ms_graph,
+                                   persistent_without_graph_records_per_s=n / (ms_nograph / 1e3),
                                    roofline_frac=frac(OPS[4]["fused"], n, ms_graph, sm_count))
-    del d, o, po, g
+    del d, o, g
     torch.cuda.empty_cache()
     # forward + backward, 64 materials, material-sorted
     mats = I.materials(5)
@@ -638,16 +696,35 @@ def other_workloads(api, N, torch, args, sm_count):
         api.eval_backward(M, d, gf, out=gp)
     ms_fb, _ = timed(fwd_bwd, max(3, steps // 2), 1)
     ms_f, _ = timed(lambda: api.eval(M, d, with_pdf=False, out=dict(f=f, status=st)), steps, 2)
+    ms_b, _ = timed(lambda: api.eval_backward(M, d, gf, out=gp), max(3, steps // 2), 1)
+    fwd_bwd_ops = tuple(a + b for a, b in zip(OPS[5]["eval"], OPS[5]["backward"]))
     # the extended parameter set (15 columns), and with the per-record
     # direction products
     ms_x, _ = timed(lambda: api.eval_backward_ext(M, d, gf), max(3, steps // 4), 1)
     ms_xd, _ = timed(lambda: api.eval_backward_ext(M, d, gf, dirs=True), max(3, steps // 8), 1)
     res[I.WORKLOAD_NAME[5]] = dict(records_per_s=n / (ms_fb / 1e3), ms=ms_fb, records=n,
+                                   roofline_frac=frac(fwd_bwd_ops, n, ms_fb, sm_count),
+                                   roofline_pipe=pipe_of(fwd_bwd_ops, n, ms_fb, sm_count),
                                    forward_only_records_per_s=n / (ms_f / 1e3),
                                    roofline_frac_forward=frac(OPS[5]["eval"], n, ms_f, sm_count),
+                                   backward_only_records_per_s=n / (ms_b / 1e3),
+                                   roofline_frac_backward=frac(OPS[5]["backward"], n, ms_b,
+                                                               sm_count),
+                                   work_per_record=dict(forward=OPS[5]["eval"],
+                                                        backward=OPS[5]["backward"],
+                                                        unit="(FP32 flops, XU ops)"),
                                    backward_ext15_records_per_s=n / (ms_x / 1e3),
                                    backward_ext15_dirs_records_per_s=n / (ms_xd / 1e3))
     return res
+
+
+def pipe_of(ops, n, ms, sm_count):
+    """The binding pipe of a roofline fraction (the larger of the two)."""
+    fl, xu = ops
+    pk = peaks(sm_count, SM_MAX_MHZ)
+    t = ms / 1e3
+    return "fp32" if fl * n / t / 1e12 / pk["fp32_tflops"] >= xu * n / t / 1e12 / pk["xu_tops"] \
+        else "xu"
 
 
 def frac(ops, n, ms, sm_count):

@@ -35,8 +35,11 @@
  * direction whose squared norm is off by more than 1e-3, material id out of
  * range, negative ratio, random number outside [0, 1)); 3 invalid sample
  * (the sampled direction left the lobe's support, e.g. total internal
- * reflection).  Sampling writes lobe << 4 | status, lobe 0 = f_x^S
- * (reflection), 1 = f_y^S (transmission), 2 = f_x^B, 3 = f_y^B.
+ * reflection); 4 not evaluated (a bounded device-side wait on a material
+ * table copy gave up; the workspace's error word says so, see
+ * bysdf_workspace_error; the record's other outputs are 0).  Sampling writes
+ * lobe << 4 | status, lobe 0 = f_x^S (reflection), 1 = f_y^S
+ * (transmission), 2 = f_x^B, 3 = f_y^B.
  *
  * Return codes: 0 ok; negative on a host-side error, in which case nothing
  * was launched (bysdf_last_error() describes it).
@@ -375,6 +378,17 @@ typedef struct bysdf_outputs {
   float* grad_params;    /* backward: [n_mat][8]                            */
 } bysdf_outputs;
 
+/* The plain per-material form of the fused op (bysdf_eval_sample_pdf): one
+ * launch per material over its sorted record range, one thread per record,
+ * tables read from global memory; eval at hits->wo and one sample from u0,
+ * u1 per record, outputs as bysdf_eval_sample_pdf (out->f_rgb, pdf, status,
+ * wo, weight, pdf_s, lobe_status; grad_params unused).  The comparison form
+ * of the fused persistent kernel.  seg_offsets_host: n_mat + 1 HOST offsets
+ * from 0 to n, non-decreasing. */
+int bysdf_plain_fused(const bysdf_materials* m, const bysdf_hits* hits,
+                      const int64_t* seg_offsets_host, const float* u0, const float* u1,
+                      int64_t n, const bysdf_outputs* out, void* stream);
+
 /* Time every supported launch shape of op (BYSDF_OP_EVAL, _SAMPLE, _PDF,
  * _FUSED, _BACKWARD) on these records with CUDA events on `stream`, keep the
  * fastest in the table for later calls and return it in *best.  Writes the
@@ -418,22 +432,41 @@ int bysdf_eval_sample_pdf_host(bysdf_host_pipeline* p, const bysdf_hits* hits, c
  * Scratch: a fixed array of BYSDF_NOALLOC_SCRATCH_BYTES in device memory,
  * defined in the library, which every GPU that loads the library holds until
  * the process exits.  It fits the tables of up to
- * (BYSDF_NOALLOC_SCRATCH_BYTES - 256) / 4 - 1 = 4031 materials; larger tables
- * return BYSDF_E_WORKSPACE.  The call allocates nothing.  Its first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
- * Every call on a device shares the one array and clears the part that must
- * start at zero; calls that may overlap on the GPU (other streams, other
- * host threads) race on it and must be serialised by the caller. */
+ * (BYSDF_NOALLOC_SCRATCH_BYTES - 256) / 4 - 1 = BYSDF_NOALLOC_MAX_MATERIALS
+ * materials; larger tables return BYSDF_E_WORKSPACE.  The call allocates
+ * nothing.  Each call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, so it stays right after a
+ * device reset; the first lookup on a device may load the library's module,
+ * so make the first call before any stream capture.  Every call on a device
+ * shares the one array and sets the part that must start at zero; calls
+ * that may overlap on the GPU (other streams, other host threads) race on
+ * it and must be serialised by the caller.  bysdf_noalloc_error reads the
+ * array's error word. */
 #define BYSDF_NOALLOC_SCRATCH_BYTES 16384
+#define BYSDF_NOALLOC_MAX_MATERIALS 4031
 int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
                        float* f_rgb, float* pdf, uint8_t* status, void* stream);
 
 /* Device-side error word of a workspace, as left by the last call that used
  * it (each call clears it first): 0 = none; bit 0: a bounded wait on a
- * shared-memory table copy gave up; bit 1: a copy was still in flight after
- * a second bounded wait.  Synchronises the stream. */
+ * shared-memory table copy gave up (the records of the tiles that could not
+ * be evaluated have status 4); bit 1: a copy was still in flight after a
+ * second bounded wait.  Synchronises the stream, then clears the word. */
 int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err);
+
+/* The error word of bysdf_eval_noalloc's fixed scratch on the current
+ * device, as bysdf_workspace_error reads a workspace's.  Synchronises
+ * the stream. */
+int bysdf_noalloc_error(void* stream, uint32_t* err);
+
+/* Test hook of the device-side error path (no counterpart in the paper):
+ * from now on, every wait on a material-table copy in the persistent kernels
+ * of `m` polls a barrier that nothing arrives on and gives up after `polls`
+ * polls, as a wait on a copy that never completes would; the real copy is
+ * then waited for (so none is in flight at exit), the error word gets bit
+ * 0 and the records get status 4.  polls = 0 switches the hook off.  No
+ * fault, no hang: every wait stays bounded. */
+int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls);
 
 #ifdef __cplusplus
 }

@@ -83,12 +83,16 @@ SYMBOLS = [
     ("bysdf_eval_backward_ext", C.c_int,
      [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_plain", C.c_int, [C.c_int, P, C.POINTER(Hits), P, P, P, C.c_int64, P, P, P, P, P, P]),
+    ("bysdf_plain_fused", C.c_int,
+     [P, C.POINTER(Hits), P, P, P, C.c_int64, C.POINTER(Outputs), P]),
     ("bysdf_set_launch_config", C.c_int, [P, C.c_int, C.POINTER(LaunchConfig)]),
     ("bysdf_get_launch_config", C.c_int, [P, C.c_int, C.POINTER(LaunchConfig)]),
     ("bysdf_autotune", C.c_int, [P, C.c_int, C.POINTER(Hits), P, P, P, C.c_int64,
                                  C.POINTER(Outputs), P, C.c_size_t, P, C.POINTER(LaunchConfig)]),
     ("bysdf_workspace_error", C.c_int, [P, P, C.POINTER(C.c_uint32)]),
     ("bysdf_eval_noalloc", C.c_int, [P, C.POINTER(Hits), C.c_int64, P, P, P, P]),
+    ("bysdf_noalloc_error", C.c_int, [P, C.POINTER(C.c_uint32)]),
+    ("bysdf_test_stall_table_waits", C.c_int, [P, C.c_uint32]),
     ("bysdf_host_pipeline_create", C.c_int, [P, C.c_int64, C.c_int, C.POINTER(P)]),
     ("bysdf_host_pipeline_destroy", C.c_int, [P]),
     ("bysdf_eval_sample_pdf_host", C.c_int,

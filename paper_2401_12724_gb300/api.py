@@ -126,6 +126,12 @@ class Materials:
         return dict(block=c.block, items=c.items, ctas_per_sm=c.ctas_per_sm,
                     occupancy=c.occupancy)
 
+    def test_stall_table_waits(self, polls: int):
+        """Test hook of the device-side error path (bysdf_test_stall_table_waits):
+        table waits give up after `polls` polls; 0 switches it off."""
+        N.check(self.lib.bysdf_test_stall_table_waits(self.handle, int(polls)),
+                "bysdf_test_stall_table_waits")
+
     def workspace_error(self, stream=None) -> int:
         err = C.c_uint32(0)
         ws = self.workspace(0)
@@ -346,6 +352,22 @@ def plain(op: int, mats: Materials, rec: dict, seg_host, stream=None, out=None) 
         _ptr(rec.get("u0")) if samp else None, _ptr(rec.get("u1")) if samp else None, n,
         _ptr(o["f"]), _ptr(o["wo"]), _ptr(o["weight"]), _ptr(o["pdf"]), _ptr(o["status"]),
         _stream(stream)), "bysdf_plain")
+    return o
+
+
+def plain_fused(mats: Materials, rec: dict, seg_host, u0=None, u1=None, stream=None,
+                out=None) -> dict:
+    """The per-material-launch form of the fused op (bysdf_plain_fused)."""
+    n = _n(rec)
+    seg = np.ascontiguousarray(seg_host, dtype=np.int64)
+    o = out if out is not None else alloc_fused(n, rec["h"].device)
+    u0 = rec["u0"] if u0 is None else u0
+    u1 = rec["u1"] if u1 is None else u1
+    outs = N.Outputs(_ptr(o["f"]), _ptr(o["pdf"]), _ptr(o["status"]), _ptr(o["wo"]),
+                     _ptr(o["weight"]), _ptr(o["pdf_s"]), _ptr(o["lobe_status"]), None)
+    N.check(mats.lib.bysdf_plain_fused(mats.handle, C.byref(hits_struct(rec)), seg.ctypes.data,
+                                       _ptr(u0), _ptr(u1), n, C.byref(outs), _stream(stream)),
+            "bysdf_plain_fused")
     return o
 
 

@@ -37,6 +37,12 @@ struct bysdf_materials {
   };
   mutable std::mutex occ_mu;
   mutable std::vector<OccEntry> occ_cache;
+  // test hook (bysdf_test_stall_table_waits): table waits of later calls poll
+  // a barrier nothing arrives on and give up after this many polls; 0 = off
+  uint32_t test_stall_polls = 0;
+  // near-field tile order: each material's rank by (plies, index), for
+  // tables of up to 32 materials
+  uint8_t mat_rank[32] = {};
 };
 
 namespace {
@@ -420,6 +426,9 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
     return fail(BYSDF_E_WORKSPACE, "workspace smaller than bysdf_workspace_size()");
   a->ctl = reinterpret_cast<WsCtl*>(ws);
   a->tile_start = reinterpret_cast<const int32_t*>((uint8_t*)ws + ws_tile_start_off());
+  std::memcpy(a->mat_rank, m->mat_rank, sizeof(a->mat_rank));
+  a->wait_limit = m->test_stall_polls ? m->test_stall_polls : kWaitLimit;
+  a->test_stall = m->test_stall_polls ? 1u : 0u;
   (void)block;
   return BYSDF_OK;
 }
@@ -511,12 +520,13 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     a.stoch_index0 = sto->index_offset;
     a.stoch_flags = sto->flags;
   }
-  // tables, then each warp's sorted tile keys (4 bytes per record of a tile)
+  // tables, then each warp's tile order list (4 bytes per record of a tile)
+  // and bucket counts
   const size_t tables = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
                                                 : (size_t)(c.block / 32) * m->stride;
   a.order_off = (int32_t)align_up(tables, 16);
   auto key_bytes = [&](int items) {
-    return items >= kSmemKeyItems ? sizeof(uint32_t) * (size_t)c.block * items : 0;
+    return sizeof(uint32_t) * (size_t)(c.block / 32) * (32 * (size_t)items + kOrderBuckets);
   };
   size_t smem = (size_t)a.order_off + key_bytes(c.items);
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
@@ -620,25 +630,23 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
 static __device__ __align__(256) uint8_t g_noalloc_scratch[BYSDF_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-std::mutex g_noalloc_mu;
-constexpr int kMaxDevices = 64;
-void* g_noalloc_addr[kMaxDevices] = {};
+// Tables of at most this many materials fit the scratch: the control words
+// and one first-tile entry per material (plus the end entry).
+constexpr int kNoallocMaxMaterials =
+    (int)((BYSDF_NOALLOC_SCRATCH_BYTES - kWsCtl) / sizeof(int32_t)) - 1;
+static_assert(BYSDF_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch in whole 256-byte units");
+static_assert(kNoallocMaxMaterials == BYSDF_NOALLOC_MAX_MATERIALS,
+              "bysdf.h states the material limit of the no-allocation call");
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// Device address of the scratch array on the current device, looked up on
+// every call with that device current (after a device reset the module, and
+// so the array, may sit elsewhere).
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  BY_CU(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(BYSDF_E_UNSUPPORTED, "device ordinal too large");
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(BYSDF_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(BYSDF_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return BYSDF_OK;
 }
 }  // namespace
@@ -752,6 +760,13 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
   M->stride = (int)stride;
   M->desc.assign(desc, desc + n);
   for (int k = 0; k < BYSDF_NOPS; ++k) M->cfg[k] = default_cfg(k);
+  if (n <= 32) {
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int x, int y) { return desc[x].n_plies < desc[y].n_plies; });
+    for (int r = 0; r < n; ++r) M->mat_rank[idx[r]] = (uint8_t)r;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   auto cleanup = [&](int rc) {
     if (M->d_table) cudaFree(M->d_table);
@@ -825,18 +840,19 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   // the forward kernels need the control words and one first-tile entry per
   // material; no per-record scratch
-  const size_t need = ws_partials_off(m->n_mat);
-  if (need > BYSDF_NOALLOC_SCRATCH_BYTES)
+  if (m->n_mat > kNoallocMaxMaterials)
     return fail(BYSDF_E_WORKSPACE, "bysdf_eval_noalloc: more materials than its fixed scratch "
-                                   "holds (at most 4031)");
+                                   "holds (at most " + std::to_string(kNoallocMaxMaterials) + ")");
+  const size_t need = ws_partials_off(m->n_mat);
   int rc = check_hits(m, hits, true, n);
   if (rc) return rc;
   if (n == 0) return BYSDF_OK;
   void* scratch = nullptr;
   if ((rc = noalloc_scratch(&scratch))) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // the previous call's contents stay in the array: zero the control words
-  BY_CU(cudaMemsetAsync(scratch, 0, kWsCtl, st));
+  // the previous call's contents stay in the array; the tile plan that
+  // starts every forward launch sets the control words (tile counter, error
+  // word) to zero, and the per-material entries are rewritten by it
   bysdf_outputs o{};
   o.f_rgb = f_rgb;
   o.pdf = pdf;
@@ -1248,6 +1264,54 @@ int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
   return BYSDF_OK;
 }
 
+int bysdf_plain_fused(const bysdf_materials* m, const bysdf_hits* hits,
+                      const int64_t* seg_offsets_host, const float* u0, const float* u1,
+                      int64_t n, const bysdf_outputs* out, void* stream) {
+  int rc = check_hits(m, hits, true, n);
+  if (rc) return rc;
+  if (!out) return fail(BYSDF_E_ARG, "out is NULL");
+  if (n == 0) return BYSDF_OK;
+  if (!seg_offsets_host) return fail(BYSDF_E_ARG, "seg_offsets_host is NULL");
+  if (seg_offsets_host[0] != 0 || seg_offsets_host[m->n_mat] != n)
+    return fail(BYSDF_E_ARG, "seg_offsets_host must run from 0 to n");
+  for (int i = 0; i < m->n_mat; ++i)
+    if (seg_offsets_host[i + 1] < seg_offsets_host[i])
+      return fail(BYSDF_E_ARG, "seg_offsets_host must be non-decreasing");
+  if ((rc = check_out(out->f_rgb, "f_rgb")) || (rc = check_out(out->status, "status")) ||
+      (rc = check_out(u0, "u0")) || (rc = check_out(u1, "u1")) ||
+      (rc = check_out(out->wo, "wo")) || (rc = check_out(out->weight, "weight")) ||
+      (rc = check_out(out->pdf_s, "pdf (sample)")) ||
+      (rc = check_out(out->lobe_status, "lobe_status")))
+    return rc;
+  if (out->pdf && !aligned16(out->pdf)) return fail(BYSDF_E_ARG, "pdf not 16-byte aligned");
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.table = m->d_table;
+  a.n_mat = m->n_mat;
+  a.stride = m->stride;
+  a.n = n;
+  a.h = hits->h;
+  a.u = hits->u;
+  a.v = hits->v;
+  a.wi = hits->wi;
+  a.wo = hits->wo;
+  a.ratio = hits->ratio;
+  a.u0 = u0;
+  a.u1 = u1;
+  a.f_rgb = out->f_rgb;
+  a.pdf = out->pdf;
+  a.status = out->status;
+  a.wo_s = out->wo;
+  a.weight_s = out->weight;
+  a.pdf_s = out->pdf_s;
+  a.lstat_s = out->lobe_status;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < m->n_mat; ++i)
+    BY_CU(launch_plain(OPF_EVAL | OPF_SAMPLE, a, i, seg_offsets_host[i], seg_offsets_host[i + 1],
+                       st));
+  return BYSDF_OK;
+}
+
 int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_config* cfg) {
   if (!m || !cfg) return fail(BYSDF_E_ARG, "NULL argument");
   if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
@@ -1319,6 +1383,20 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
   m->cfg[op] = best_c;
   m->cfg_set[op] = true;
   *best = best_c;
+  return BYSDF_OK;
+}
+
+int bysdf_noalloc_error(void* stream, uint32_t* err) {
+  if (!err) return fail(BYSDF_E_ARG, "NULL argument");
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  return bysdf_workspace_error(scratch, stream, err);
+}
+
+int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  m->test_stall_polls = polls;
   return BYSDF_OK;
 }
 

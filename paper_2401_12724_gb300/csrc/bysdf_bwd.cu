@@ -17,7 +17,7 @@ template <int BLOCK, int MINB, bool EXT>
 __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
   constexpr int NP = EXT ? 15 : 8;
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint64_t bars[BLOCK / 32];
+  __shared__ uint64_t bars[2 * (BLOCK / 32)];
   // MODE_ALL_SMEM: per-CTA accumulators behind the tables
   float* sacc = reinterpret_cast<float*>(smem + (size_t)a.n_mat * a.stride);
   if (a.mode == MODE_ALL_SMEM) {
@@ -150,7 +150,7 @@ __device__ __forceinline__ void dirgrad_record(const KArgs& a, const MatDev& m,
 template <int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint64_t bars[BLOCK / 32];
+  __shared__ uint64_t bars[2 * (BLOCK / 32)];
   persistent_loop<BLOCK>(a, smem, bars,
                              [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane,
                                  int) {

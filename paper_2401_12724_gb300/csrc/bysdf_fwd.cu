@@ -55,6 +55,9 @@ cudaError_t launch_plain(int op, const KArgs& a, int mat, int64_t begin, int64_t
     case OPF_EVAL: k_plain<OPF_EVAL><<<grid, 256, 0, st>>>(a, mat, begin, end); break;
     case OPF_SAMPLE: k_plain<OPF_SAMPLE><<<grid, 256, 0, st>>>(a, mat, begin, end); break;
     case OPF_PDF: k_plain<OPF_PDF><<<grid, 256, 0, st>>>(a, mat, begin, end); break;
+    case OPF_EVAL | OPF_SAMPLE:
+      k_plain<OPF_EVAL | OPF_SAMPLE><<<grid, 256, 0, st>>>(a, mat, begin, end);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

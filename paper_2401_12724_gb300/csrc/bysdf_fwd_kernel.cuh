@@ -10,30 +10,22 @@ namespace bysdf {
 template <int OP, int BLOCK, int ITEMS, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint64_t bars[BLOCK / 32];
+  __shared__ uint64_t bars[2 * (BLOCK / 32)];
   constexpr bool kWo = (OP & (OPF_EVAL | OPF_PDF)) != 0;
   constexpr bool kU = (OP & OPF_SAMPLE) != 0;
+  // each warp's order list (32 * ITEMS entries) and bucket counts (32)
+  // behind the tables
+  uint32_t* list = reinterpret_cast<uint32_t*>(smem + a.order_off) +
+                   (threadIdx.x >> 5) * (32 * ITEMS + kOrderBuckets);
+  uint32_t* hist = list + 32 * ITEMS;
   persistent_loop<BLOCK>(a, smem, bars,
                          [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane, int) {
-    uint32_t order[ITEMS];
-    tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, order);
-    // from 4 records per lane on, the sorted keys wait in shared memory while
-    // the records run, which frees their registers (each lane reads back only
-    // its own slots, so no synchronisation is needed)
-    uint32_t* keys = nullptr;
-    if constexpr (ITEMS >= kSmemKeyItems) {
-      keys = reinterpret_cast<uint32_t*>(smem + a.order_off) + (threadIdx.x >> 5) * (32 * ITEMS);
-#pragma unroll
-      for (int j = 0; j < ITEMS; ++j) keys[j * 32 + lane] = order[j];
-    }
+    tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, list, hist);
+    // rounds in bucket order; each lane reads back only its own slots of the
+    // list, written before the warp's last synchronisation
 #pragma unroll 1
     for (int j = 0; j < ITEMS; ++j) {
-      uint32_t e;
-      if constexpr (ITEMS >= kSmemKeyItems) {
-        e = keys[j * 32 + lane];
-      } else {
-        e = pick<ITEMS>(order, j);
-      }
+      const uint32_t e = list[j * 32 + lane];
       if (e == 0xffffffffu) continue;
       const int64_t i = begin + (e & 0xffu);
       Record q;
@@ -51,6 +43,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
       forward_record<OP, (BLOCK * MINB <= 512 ? 2 : 1)>(
           a, *m, reinterpret_cast<const float2*>(m + 1), i, q);
     }
+    __syncwarp();   // the list is rewritten by the next tile
   });
 }
 

@@ -45,7 +45,10 @@ struct KArgs {
   uint64_t stoch_seed;       // stochastic estimators: generator key word 0,
   int64_t stoch_index0;      //   global index of record 0,
   uint32_t stoch_flags;      //   STOCH_* bits
+  uint32_t wait_limit;       // polls of a table-copy wait before it gives up
+  uint32_t test_stall;       // test hook: table waits poll a barrier nothing arrives on
   uint32_t pad_st;
+  uint8_t mat_rank[32];      // near-field tile order: material rank by (N_p, index), n_mat <= 32
   WsCtl* ctl;
   const int32_t* tile_start;
 };
@@ -91,9 +94,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: gives up after `limit` polls (each poll may itself suspend
 // for a hardware-defined interval), records the failure and returns false.
+constexpr uint32_t kWaitLimit = 1u << 22;
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, WsCtl* ctl,
-                                                  uint32_t code) {
-  const uint32_t limit = 1u << 22;
+                                                  uint32_t code, uint32_t limit = kWaitLimit) {
   for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   atomicOr(&ctl->err, code);
@@ -273,6 +276,27 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   }
 }
 
+// Records of a tile no warp could evaluate (a table wait gave up): every
+// per-record output gets a defined value, status ST_ABORTED and zeros, so a
+// caller never reads a previous call's contents as this call's results.
+__device__ __forceinline__ void abort_tile(const KArgs& a, int64_t begin, int64_t end, int lane) {
+  const int64_t n = a.n;
+  for (int64_t i = begin + lane; i < end; i += 32) {
+    if (a.status) a.status[i] = (uint8_t)ST_ABORTED;
+    if (a.lstat_s) a.lstat_s[i] = (uint8_t)ST_ABORTED;
+    if (a.pdf) a.pdf[i] = 0.f;
+    if (a.pdf_s) a.pdf_s[i] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (a.f_rgb) a.f_rgb[c * n + i] = 0.f;
+      if (a.wo_s) a.wo_s[c * n + i] = 0.f;
+      if (a.weight_s) a.weight_s[c * n + i] = 0.f;
+      if (a.grad_wi) a.grad_wi[c * n + i] = 0.f;
+      if (a.grad_wo) a.grad_wo[c * n + i] = 0.f;
+    }
+  }
+}
+
 // Shared-memory staging of the material tables and the warp tile loop, common
 // to the forward and backward persistent kernels.
 //
@@ -282,27 +306,39 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
 //   slot and refills it (TMA bulk copy) when its tile's material changes.
 // Work is handed out one warp tile (32 * items records) at a time from an
 // atomic counter, so warps that drew cheap records take more tiles.
+//
+// Every wait on a table copy is bounded.  When one gives up, the error word
+// records it, the copy is waited for once more (so that none is in flight
+// when the CTA exits), and the warps keep taking tiles but only mark their
+// records ST_ABORTED.  bars holds 2 * BLOCK / 32 barriers: the second half
+// are the barriers of the test hook (a.test_stall), which nothing arrives on.
 template <int BLOCK, class Body>
 __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, uint64_t* bars,
                                                 Body&& body) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* stall = bars + BLOCK / 32;
+  const uint32_t limit = a.wait_limit ? a.wait_limit : kWaitLimit;
   __shared__ int s_ok;
+  bool aborted = false;
   if (a.mode == MODE_ALL_SMEM) {
     if (threadIdx.x == 0) {
       mbar_init(&bars[0], 1);
+      mbar_init(&stall[0], 1);
       fence_mbar_init();
       const uint32_t bytes = (uint32_t)a.n_mat * (uint32_t)a.stride;
       mbar_arrive_tx(&bars[0], bytes);
       bulk_g2s(smem, a.table, bytes, &bars[0]);
-      int ok = mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_WAIT);
+      int ok = mbar_wait_bounded(a.test_stall ? &stall[0] : &bars[0], 0, a.ctl, ERR_TABLE_WAIT,
+                                 limit);
       if (!ok) mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_INFLIGHT);
       s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) return;
+    aborted = !s_ok;
   } else {
     if (lane == 0) {
       mbar_init(&bars[warp], 1);
+      mbar_init(&stall[warp], 1);
       fence_mbar_init();
     }
     __syncwarp();
@@ -336,22 +372,29 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
       begin = s0 + (int64_t)(tile - __ldg(a.tile_start + mat)) * a.tile;
       end = begin + a.tile < s1 ? begin + a.tile : s1;
       if (end < begin) end = begin;
-      if (mat != cur) {
+      if (!aborted && mat != cur) {
         __syncwarp();
         if (lane == 0) {
           fence_proxy_async();
           mbar_arrive_tx(&bars[warp], (uint32_t)a.stride);
           bulk_g2s(slot, a.table + (size_t)mat * a.stride, (uint32_t)a.stride, &bars[warp]);
         }
-        bool ok = mbar_wait_bounded(&bars[warp], parity, a.ctl, ERR_TABLE_WAIT);
+        bool ok = mbar_wait_bounded(a.test_stall ? &stall[warp] : &bars[warp], parity, a.ctl,
+                                    ERR_TABLE_WAIT, limit);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) {
           if (lane == 0) mbar_wait_bounded(&bars[warp], parity, a.ctl, ERR_TABLE_INFLIGHT);
-          break;
+          __syncwarp();
+          aborted = true;
+        } else {
+          parity ^= 1u;
+          cur = mat;
         }
-        parity ^= 1u;
-        cur = mat;
       }
+    }
+    if (aborted) {
+      abort_tile(a, begin, end, lane);
+      continue;
     }
     body(begin, end, mat, slot, lane, tile);
   }
@@ -360,54 +403,40 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
 // ---------------------------------------------------- work order in a tile --
 // Lanes of a warp run in lock step, so a round costs as much as its most
 // expensive record (most plies, most footprint nodes).  The records of a warp
-// tile are therefore taken in order of their loop structure, K footprint
-// nodes then N_p plies (records of one round run the same node and ply
-// loops), then of material (so that the lanes of a round mostly read one
-// table), by a bitonic sort of (cost << 16 | material << 8 | index) keys
-// across the warp (ITEMS keys per lane; element e = j * 32 + lane lives in
-// v[j] of lane `lane`).  Empty slots hold 0xffffffff and sort last.
-template <int ITEMS>
-__device__ __forceinline__ void warp_bitonic_sort(uint32_t (&v)[ITEMS], int lane) {
-  constexpr int N = 32 * ITEMS;
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int s = k >> 1; s > 0; s >>= 1) {
-      if (s < 32) {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-          const int e = j * 32 + lane;
-          const uint32_t o = __shfl_xor_sync(0xffffffffu, v[j], s);
-          const bool up = (e & k) == 0;
-          const bool lower = (e & s) == 0;
-          v[j] = (lower == up) ? min(v[j], o) : max(v[j], o);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-          const int jj = j ^ (s >> 5);
-          if (jj > j) {
-            const bool up = ((j * 32 + lane) & k) == 0;
-            const uint32_t x = v[j], y = v[jj];
-            v[j] = up ? min(x, y) : max(x, y);
-            v[jj] = up ? max(x, y) : min(x, y);
-          }
-        }
-      }
-    }
-  }
+// tile are therefore taken in order of their loop structure: each record
+// gets a bucket in [0, 32) and the tile is split into its buckets in
+// ascending order.  The split is a counting sort across the warp: lanes
+// holding the same bucket are found by a match, one leader per group adds
+// the group to the bucket's count in shared memory, a warp scan of the
+// counts gives each bucket's start, and every record is written to its
+// place in the warp's order list (element e = j * 32 + lane is item j of
+// lane `lane`; ITEMS items per lane; records past the tile's end are
+// listed as empty).
+constexpr int kOrderBuckets = 32;
+
+// Records with a footprint: footprint nodes K (up to 16 told apart), then
+// N_p above or below 4.  Near-field calls: the material's rank in (N_p,
+// index) order, so that a round holds one material where it can (up to 32
+// materials; beyond, N_p then the material's low two bits).
+__device__ __forceinline__ uint32_t record_bucket(const KArgs& a, int K, int np, int mm) {
+  if (a.ratio) return (uint32_t)(((K < 16 ? K : 16) - 1) * 2 + (np > 3 ? 1 : 0));
+  if (a.n_mat <= kOrderBuckets) return a.mat_rank[mm];
+  return (uint32_t)(((np < 8 ? np : 8) - 1) * 4 + (mm & 3));
 }
 
 template <int ITEMS>
 __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, int64_t begin,
                                            int64_t end, int mat, const uint8_t* slot, int lane,
-                                           uint32_t (&v)[ITEMS]) {
+                                           uint32_t* list, uint32_t* hist) {
+  uint32_t b[ITEMS];
+  bool valid[ITEMS];
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const int idx = j * 32 + lane;
     const int64_t i = begin + idx;
-    v[j] = 0xffffffffu;
-    if (i < end) {
+    b[j] = kOrderBuckets - 1;
+    valid[j] = i < end;
+    if (valid[j]) {
       const MatDev* m;
       int mm = 0;
       if (mat >= 0) {
@@ -419,24 +448,38 @@ __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, 
       }
       int K = 1;
       if (a.ratio) K = footprint(__ldcg(a.h + i), __ldcg(a.ratio + i), m->kmax).K;
-      const uint32_t cost = (uint32_t)((K << 4) | m->np);  // K <= 64, N_p <= 8
-      v[j] = (cost << 16) | ((uint32_t)(mm & 0xff) << 8) | (uint32_t)idx;
+      b[j] = record_bucket(a, K, m->np, mm);
     }
   }
-  warp_bitonic_sort<ITEMS>(v, lane);
-}
-
-// tiles of at least this many records per lane keep their sorted keys in
-// shared memory (kSmemKeyItems * 4 bytes per thread, behind the tables)
-constexpr int kSmemKeyItems = 4;
-
-template <int ITEMS>
-__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[ITEMS], int j) {
-  uint32_t e = v[0];
+  hist[lane] = 0u;
+  __syncwarp();
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t rank[ITEMS];
 #pragma unroll
-  for (int jj = 1; jj < ITEMS; ++jj)
-    if (jj == j) e = v[jj];
-  return e;
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, b[j]);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&hist[b[j]], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    rank[j] = base + (uint32_t)__popc(peers & lt);
+  }
+  __syncwarp();
+  // exclusive scan of the bucket counts (lane = bucket)
+  const uint32_t h = hist[lane];
+  uint32_t incl = h;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t start = incl - h;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t pos = __shfl_sync(0xffffffffu, start, (int)b[j]) + rank[j];
+    list[pos] = valid[j] ? (uint32_t)(j * 32 + lane) : 0xffffffffu;
+  }
+  __syncwarp();
 }
 
 }  // namespace bysdf

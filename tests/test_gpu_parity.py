@@ -2,7 +2,8 @@
 element by element on seeded inputs shaped like the five workloads, at sizes
 the oracle finishes in seconds (several warp tiles plus a ragged tail), and
 on sampled records of the full-size workloads in the benchmark's launch
-configuration.  See parity_util for the tolerance and the conditioning rule."""
+configuration.  See oracle/parity.py for the tolerance and the rule: strict
+on every well-conditioned record, the oracle's bracket elsewhere."""
 import numpy as np
 import pytest
 
@@ -29,35 +30,57 @@ def np_(t):
     return t.detach().cpu().numpy()
 
 
-def check_eval(orc, api, mats_desc, rec, seg=None, name="eval", min_strict=0.98,
-               max_outside=0.002):
+def eval_view(orc, mats, rec, **kw):
+    """The oracle's eval (f, pdf, status) at the records and next to them."""
+    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
+    return PU.oracle_view(orc, fn, mats, rec, **kw)
+
+
+def check_eval_against(view, f, p, st, name):
+    PU.assert_status(st, view, name)
+    r1 = PU.assert_parity(f, view, 0, name + ".f", gpu_status=st)
+    r2 = PU.assert_parity(p, view, 1, name + ".pdf", gpu_status=st)
+    return r1, r2
+
+
+def check_eval(orc, api, mats_desc, rec, seg=None, name="eval"):
     M = api.Materials(mats_desc)
     d = dev(api, rec, seg)
     f, p, st = api.eval(M, d)
     torch.cuda.synchronize()
     f, p, st = np_(f), np_(p), np_(st)
     PU.dump(name, f=f, p=p, st=st, **{"rec_" + k: v for k, v in rec.items()})
-    fn = lambda r: orc.eval_records(mats_desc, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, rec)
-    PU.assert_status(st, sb, [q[2] for q in pert], name)
-    r1 = PU.assert_parity(f, fb, [q[0] for q in pert], name + ".f", min_strict, max_outside)
-    r2 = PU.assert_parity(p, pb, [q[1] for q in pert], name + ".pdf", min_strict, max_outside)
+    view = eval_view(orc, mats_desc, rec)
+    r = check_eval_against(view, f, p, st, name)
     assert M.workspace_error() == 0
-    return M, d, (f, p, st), (fb, pb, sb), (r1, r2)
+    return M, d, (f, p, st), view.base, r
+
+
+def sample_view(orc, mats, rec, fn=None, **kw):
+    """The oracle's sample (wo, weight, pdf, status | lobe << 4)."""
+    fn0 = fn or (lambda r: orc.sample_records(mats, r, threads=8))
+
+    def code(r):
+        wo, w, p, s, lb = fn0(r)
+        return wo, w, p, s | (lb << 4)
+    return PU.oracle_view(orc, code, mats, rec, sample=True, values=(1, 2), status_idx=3,
+                          angle_idx=0, **kw)
+
+
+def check_sample_against(view, wo, w, ps, ls, name):
+    PU.assert_status(ls, view, name + ".lobe_status")
+    wob = view.base[0]
+    both_ok = ((view.base[3] & 15) == 0) & ((ls & 15) == 0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ang = np.where(both_ok, PU.angle_between(wo, wob), 0.0)
+    PU.assert_parity(wo, view, 0, name + ".wo", err=ang / PU.ANGLE, gpu_status=ls,
+                     direction=True)
+    PU.assert_parity(w, view, 1, name + ".weight", gpu_status=ls)
+    PU.assert_parity(ps, view, 2, name + ".pdf", gpu_status=ls)
 
 
 def check_sample(orc, mats, rec, wo, w, ps, ls, name):
-    fn = lambda r: orc.sample_records(mats, r, threads=8)  # noqa: E731
-    base, pert = PU.conditioning(fn, rec, sample=True)
-    wob, wb, pb_s, sb_s, lb = base
-    code_b = sb_s | (lb << 4)
-    PU.assert_status(ls, code_b, [q[3] | (q[4] << 4) for q in pert], name + ".lobe_status")
-    both_ok = (sb_s == 0) & ((ls & 15) == 0)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        ang = np.where(both_ok, PU.angle_between(wo, wob), 0.0)
-    PU.assert_parity(wo, wob, [q[0] for q in pert], name + ".wo", err=ang / PU.ANGLE)
-    PU.assert_parity(w, wb, [q[1] for q in pert], name + ".weight")
-    PU.assert_parity(ps, pb_s, [q[2] for q in pert], name + ".pdf")
+    check_sample_against(sample_view(orc, mats, rec), wo, w, ps, ls, name)
 
 
 def test_eval_near_field_one_material(orc, api):
@@ -134,8 +157,16 @@ def test_sorted_many_materials_and_plain_form(orc, api):
     check_sample(orc, mats, rec, wo, w, ps, ls, "c4.sample")
     o2 = api.plain(1, M, d, seg)
     torch.cuda.synchronize()
-    check_sample(orc, mats, rec, np_(o2["wo"]), np_(o2["weight"]), np_(o2["pdf"]),
-                 np_(o2["status"]), "c4.plain_sample")
+    sv = sample_view(orc, mats, rec)
+    check_sample_against(sv, np_(o2["wo"]), np_(o2["weight"]), np_(o2["pdf"]),
+                         np_(o2["status"]), "c4.plain_sample")
+    # the fused op in the plain per-material form, against the oracle
+    o3 = api.plain_fused(M, d, seg)
+    torch.cuda.synchronize()
+    ev = eval_view(orc, mats, rec)
+    check_eval_against(ev, np_(o3["f"]), np_(o3["pdf"]), np_(o3["status"]), "c4.plain_fused")
+    check_sample_against(sv, np_(o3["wo"]), np_(o3["weight"]), np_(o3["pdf_s"]),
+                         np_(o3["lobe_status"]), "c4.plain_fused.sample")
     # every launch shape gives the same answer up to the rounding of another
     # instantiation (steep spots of the fiber phase amplify it)
     for block, items in ((128, 1), (512, 4)):
@@ -166,11 +197,7 @@ def test_sorted_footprint_records(orc, api, n):
     f, p, st = (np_(t) for t in api.eval(M, dev(api, rec, seg)))
     idx = np.sort(np.random.default_rng(3).choice(n, 3000, replace=False))
     sub = {k: v[..., idx] for k, v in rec.items()}
-    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, sub)
-    PU.assert_status(st[idx], sb, [q[2] for q in pert], "sorted_fp_big.status")
-    PU.assert_parity(f[:, idx], fb, [q[0] for q in pert], "sorted_fp_big.f")
-    PU.assert_parity(p[idx], pb, [q[1] for q in pert], "sorted_fp_big.pdf")
+    check_eval_against(eval_view(orc, mats, sub), f[:, idx], p[idx], st[idx], "sorted_fp_big")
     assert M.workspace_error() == 0
 
 
@@ -182,10 +209,9 @@ def test_backward_matches_oracle_gradient(orc, api, sorted_mode):
     rec["ratio"] = np.where(np.arange(n) % 3 == 0, 0.4, 0.0).astype(np.float32)
     seg = I.seg_offsets_from_ids(rec["mat_id"], 12) if sorted_mode else None
     g = np.random.default_rng(52).uniform(-1, 1, (3, n)).astype(np.float32)
-    # records on a branch have no unique derivative: give them no weight
-    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, rec)
-    good = PU.stable_mask([fb], [(q[0],) for q in pert], sb, [q[2] for q in pert])
+    # records on a branch or at a steep spot have no derivative the float32
+    # path can follow: give them no weight
+    good = eval_view(orc, mats, rec).stable
     g[:, ~good] = 0.0
     grad_o, _, J = orc.grad_records(mats, rec, g.astype(np.float64), threads=8, jac=True)
     scale = np.zeros((12, 8))
@@ -229,9 +255,9 @@ def test_extended_backward_matches_oracle(orc, api, sorted_mode):
     rec["ratio"] = np.where(np.arange(n) % 3 == 0, 0.4, 0.0).astype(np.float32)
     seg = I.seg_offsets_from_ids(rec["mat_id"], 12) if sorted_mode else None
     g = np.random.default_rng(54).uniform(-1, 1, (3, n)).astype(np.float32)
-    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, rec)
-    good = PU.stable_mask([fb], [(q[0],) for q in pert], sb, [q[2] for q in pert])
+    view = eval_view(orc, mats, rec)
+    good = view.stable
+    sb = view.base[2]
     g[:, ~good] = 0.0
     grad_o, gwi_o, gwo_o, _, J = orc.grad_ext_records(mats, rec, g.astype(np.float64),
                                                       threads=8, jac=True)
@@ -253,12 +279,15 @@ def test_extended_backward_matches_oracle(orc, api, sorted_mode):
         share = ok[:, good].all(axis=0).mean()
         assert share >= 0.99, share
         assert np.all(got[:, sb != 0] == 0)
-    # the 8-parameter call: albedo moves both body colours (tied materials)
+    # the 8-parameter call: albedo moves both body colours (tied materials);
+    # another instantiation, whose float32 atomics add in another order: the
+    # same per-material bound as against the oracle
     g8 = np_(api.eval_backward(M, d, gt))
     tied = np.array([("albedo_y" not in m) for m in mats])
-    np.testing.assert_allclose(g8[tied, 0:3], (gp[:, 0:3] + gp[:, 9:12])[tied], rtol=1e-4,
-                               atol=1e-5)
-    np.testing.assert_allclose(g8[:, 3:8], gp[:, 3:8], rtol=1e-4, atol=1e-5)
+    sc8 = scale[:, 0:3] + scale[:, 9:12]
+    assert (np.abs(g8[tied, 0:3] - (gp[:, 0:3] + gp[:, 9:12])[tied])
+            <= 2e-4 * sc8[tied] + 1e-5).all()
+    assert (np.abs(g8[:, 3:8] - gp[:, 3:8]) <= 2e-4 * scale[:, 3:8] + 1e-5).all()
     if sorted_mode:
         a, _, _ = api.eval_backward_ext(M, d, gt, deterministic=True)
         b, _, _ = api.eval_backward_ext(M, d, gt, deterministic=True)
@@ -345,10 +374,9 @@ def test_stochastic_estimators_match_oracle(orc, api, flags):
     PU.dump(f"stoch_{flags}", f=f, p=p, st=st, **{"rec_" + k: v for k, v in rec.items()})
     fn = lambda r: orc.eval_stochastic_records(mats, r, seed, flags, index_offset=off,  # noqa
                                                 threads=8)
-    (fb, pb, sb), pert = PU.conditioning(fn, rec)
-    PU.assert_status(st, sb, [q[2] for q in pert], f"stoch{flags}")
-    PU.assert_parity(f, fb, [q[0] for q in pert], f"stoch{flags}.f")
-    PU.assert_parity(p, pb, [q[1] for q in pert], f"stoch{flags}.pdf")
+    mk = dict(seed=seed, flags=flags, index_offset=off)
+    view = PU.oracle_view(orc, fn, mats, rec, margin_kw=mk)
+    check_eval_against(view, f, p, st, f"stoch{flags}")
     # the estimate moved away from the deterministic one
     f_det = np_(api.eval(M, d)[0])
     assert (np.abs(f - f_det) > 1e-3 * (np.abs(f_det) + 1e-3)).any(axis=0).mean() > 0.05
@@ -356,22 +384,15 @@ def test_stochastic_estimators_match_oracle(orc, api, flags):
     # stochastic eval, its sample matches the oracle's stochastic sample
     o = api.eval_sample_pdf_stochastic(M, d, seed, flags, index_offset=off)
     fo = np_(o["f"])
-    PU.assert_parity(fo, fb, [q[0] for q in pert], f"stoch{flags}.fused_f")
+    PU.assert_parity(fo, view, 0, f"stoch{flags}.fused_f", gpu_status=np_(o["status"]))
     # another instantiation rounds differently: agreement with the eval call
     # up to float32 rounding except at steep spots
     assert np.isclose(fo, f, rtol=1e-5, atol=1e-7).all(axis=0).mean() >= 0.999
     fn_s = lambda r: orc.sample_stochastic_records(mats, r, seed, flags,  # noqa: E731
                                                     index_offset=off, threads=8)
-    base, pert = PU.conditioning(fn_s, rec, sample=True)
-    wob, wb, pb_s, sb_s, lb = base
+    sview = sample_view(orc, mats, rec, fn=fn_s, margin_kw=mk)
     wo, w, ps, ls = np_(o["wo"]), np_(o["weight"]), np_(o["pdf_s"]), np_(o["lobe_status"])
-    PU.assert_status(ls, sb_s | (lb << 4), [q[3] | (q[4] << 4) for q in pert], "stoch.ls")
-    both_ok = (sb_s == 0) & ((ls & 15) == 0)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        ang = np.where(both_ok, PU.angle_between(wo, wob), 0.0)
-    PU.assert_parity(wo, wob, [q[0] for q in pert], "stoch.wo", err=ang / PU.ANGLE)
-    PU.assert_parity(w, wb, [q[1] for q in pert], "stoch.weight")
-    PU.assert_parity(ps, pb_s, [q[2] for q in pert], "stoch.pdf_s")
+    check_sample_against(sview, wo, w, ps, ls, f"stoch{flags}.sample")
 
 
 def test_stochastic_options_and_sharding(api):
@@ -421,9 +442,7 @@ def test_fiber_migration_matches_oracle(orc, api, sorted_mode):
     check_sample(orc, mats, rec, wo, w, ps, ls, name + ".sample")
     # backward: the helix angles move the blend weights and the maps' phases
     g = np.random.default_rng(96).uniform(-1, 1, (3, rec["h"].shape[0])).astype(np.float32)
-    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb2, _, sb2), pert = PU.conditioning(fn, rec)
-    good = PU.stable_mask([fb2], [(q[0],) for q in pert], sb2, [q[2] for q in pert])
+    good = eval_view(orc, mats, rec).stable
     g[:, ~good] = 0.0
     grad_o, _, J = orc.grad_records(mats, rec, g.astype(np.float64), threads=8, jac=True)
     scale = np.zeros((n_mat, 8))
@@ -466,13 +485,14 @@ def test_autograd_function_and_fitting(orc, api):
     err0 = (start.cuda() - theta_star[:, free]).abs().mean()
     err1 = (x.detach() - theta_star[:, free]).abs().mean()
     assert err1 < 0.5 * err0, (float(err0), float(err1))
-    # backward through autograd equals the direct call
+    # backward through autograd equals the direct call (bit for bit in the
+    # deterministic, fixed-order mode; the atomic mode adds in another order)
     th = theta_star.clone().requires_grad_(True)
-    f, _ = api.bysdf(th, M, d)
+    f, _ = api.bysdf(th, M, d, deterministic=True)
     gout = torch.randn_like(f)
     f.backward(gout)
-    direct = api.eval_backward(M, d, gout.contiguous())
-    torch.testing.assert_close(th.grad, direct, rtol=1e-5, atol=1e-6)
+    direct = api.eval_backward(M, d, gout.contiguous(), deterministic=True)
+    torch.testing.assert_close(th.grad, direct, rtol=0, atol=0)
 
 
 def test_edge_cases(orc, api):
@@ -513,7 +533,7 @@ def test_edge_cases(orc, api):
     # texels on one radian of ply azimuth: the fiber phase is a few hundred
     # times steeper than in the workloads, so fewer records stay within
     # float32 reach of the tolerance
-    check_eval(orc, api, big, r, name="max-shapes", min_strict=0.8, max_outside=0.005)
+    check_eval(orc, api, big, r, name="max-shapes")
     # 64 cross-section updates: where the iteration does not contract (rays
     # nearly along the yarn) 64 steps turn rounding into a different orbit,
     # so only validity and status are checked there
@@ -542,11 +562,8 @@ def test_full_size_sampled_records(orc, api, cfg):
     sub = {k: v[..., idx] for k, v in rec.items()}
     PU.dump(f"full{cfg}", idx=idx, f=np_(o["f"])[:, idx], p=np_(o["pdf"])[idx],
             st=np_(o["status"])[idx])
-    fn = lambda r: orc.eval_records(mats, r, threads=8)  # noqa: E731
-    (fb, pb, sb), pert = PU.conditioning(fn, sub)
-    PU.assert_status(np_(o["status"])[idx], sb, [q[2] for q in pert], "full.status")
-    PU.assert_parity(np_(o["f"])[:, idx], fb, [q[0] for q in pert], "full.f")
-    PU.assert_parity(np_(o["pdf"])[idx], pb, [q[1] for q in pert], "full.pdf")
+    check_eval_against(eval_view(orc, mats, sub), np_(o["f"])[:, idx], np_(o["pdf"])[idx],
+                       np_(o["status"])[idx], f"full{cfg}")
     # property at full size: every record has a status and finite outputs
     st = np_(o["status"])
     assert set(np.unique(st)) <= {0, 1, 2, 3}

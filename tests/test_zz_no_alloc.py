@@ -69,9 +69,32 @@ def test_noalloc_eval_matches_eval_twice(mods):
         M.close()
 
 
+def header_define(name):
+    import os
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                       "bysdf.h")
+    return int(re.search(rf"#define {name} (\d+)", open(hdr).read()).group(1))
+
+
+def test_noalloc_error_word_reads_zero_after_a_normal_call(mods):
+    api, lib = mods
+    mats, rec, seg = next(cases())
+    M = api.Materials(mats)
+    noalloc_eval(api, lib, M, api.records_to_device(rec, "cuda", seg))
+    err = C.c_uint32(123)
+    assert lib.bysdf_noalloc_error(None, C.byref(err)) == 0
+    assert err.value == 0
+    M.close()
+
+
 def test_noalloc_refuses_tables_beyond_its_scratch(mods):
     api, lib = mods
-    n_mat = 4032            # one more than the fixed scratch holds
+    # the fixed scratch holds the 256-byte control block and one 4-byte
+    # first-tile entry per material plus an end entry
+    limit = (header_define("BYSDF_NOALLOC_SCRATCH_BYTES") - 256) // 4 - 1
+    assert limit == header_define("BYSDF_NOALLOC_MAX_MATERIALS")
+    n_mat = limit + 1       # one more than the fixed scratch holds
     mats = [I.material(flags=1)] * n_mat
     M = api.Materials(mats)
     rec = I.random_records(64, seed=92, wi_mode="cosine")
@@ -84,5 +107,5 @@ def test_noalloc_refuses_tables_beyond_its_scratch(mods):
     rc = lib.bysdf_eval_noalloc(M.handle, C.byref(api.hits_struct(d)), 64, f.data_ptr(),
                                 p.data_ptr(), st.data_ptr(), None)
     assert rc == -4
-    assert "4031" in lib.bysdf_last_error().decode()
+    assert f"at most {limit}" in lib.bysdf_last_error().decode()
     M.close()

@@ -199,10 +199,19 @@ def cpu_oracle_rate(cfg: int, target_s: float = 10.0, max_records: int = CHECK_R
         dt = time.perf_counter() - t0
         if dt >= target_s:
             break
+    # one thread, on a shorter prefix
+    n1 = 1 << 15
+    rec1 = I.records(cfg, 0, n1)
+    t1 = time.perf_counter()
+    oracle.eval_records(mats, rec1, threads=1)
+    oracle.sample_records(mats, rec1, threads=1)
+    dt1 = time.perf_counter() - t1
     return dict(value=done / dt, unit=UNIT, cores=threads, kind="oracle",
                 sample=f"first {n} records of workload {I.WORKLOAD_NAME[cfg]}, eval(+pdf) and "
                        f"one sample each, FP64, {threads} threads, {done // n} passes",
-                seconds=dt, records=done), first
+                seconds=dt, records=done,
+                single_thread=dict(value=n1 / dt1, unit=UNIT, cores=1, records=n1,
+                                   seconds=dt1)), first
 
 
 def parity_rule(gpu: dict, cfg: int) -> dict:
@@ -487,6 +496,10 @@ def main():
                 warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload=I.WORKLOAD_NAME[cfg], records=n, materials=len(mats),
+                            headline="the metric's quoted workload: eval + importance sample + "
+                                     "pdf over 8 yarn materials, 2^24 records; the 2^26-record "
+                                     "256-material batch and the other workloads are in "
+                                     "'workloads'",
                             step="fused eval(+pdf at wo) + one importance sample per record",
                             l2="inputs larger than L2 (~0.8 GB of records per step)",
                             launch=M.launch_config(N.OP_FUSED),

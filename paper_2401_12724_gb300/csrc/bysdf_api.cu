@@ -40,9 +40,6 @@ struct bysdf_materials {
   // test hook (bysdf_test_stall_table_waits): table waits of later calls poll
   // a barrier nothing arrives on and give up after this many polls; 0 = off
   uint32_t test_stall_polls = 0;
-  // near-field tile order: each material's rank by (plies, index), for
-  // tables of up to 32 materials
-  uint8_t mat_rank[32] = {};
 };
 
 namespace {
@@ -426,7 +423,6 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
     return fail(BYSDF_E_WORKSPACE, "workspace smaller than bysdf_workspace_size()");
   a->ctl = reinterpret_cast<WsCtl*>(ws);
   a->tile_start = reinterpret_cast<const int32_t*>((uint8_t*)ws + ws_tile_start_off());
-  std::memcpy(a->mat_rank, m->mat_rank, sizeof(a->mat_rank));
   a->wait_limit = m->test_stall_polls ? m->test_stall_polls : kWaitLimit;
   a->test_stall = m->test_stall_polls ? 1u : 0u;
   (void)block;
@@ -760,13 +756,6 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
   M->stride = (int)stride;
   M->desc.assign(desc, desc + n);
   for (int k = 0; k < BYSDF_NOPS; ++k) M->cfg[k] = default_cfg(k);
-  if (n <= 32) {
-    std::vector<int> idx(n);
-    for (int i = 0; i < n; ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](int x, int y) { return desc[x].n_plies < desc[y].n_plies; });
-    for (int r = 0; r < n; ++r) M->mat_rank[idx[r]] = (uint8_t)r;
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   auto cleanup = [&](int rc) {
     if (M->d_table) cudaFree(M->d_table);

@@ -20,12 +20,19 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
   uint32_t* hist = list + 32 * ITEMS;
   persistent_loop<BLOCK>(a, smem, bars,
                          [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane, int) {
-    tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, list, hist);
-    // rounds in bucket order; each lane reads back only its own slots of the
-    // list, written before the warp's last synchronisation
+    // records with a footprint in bucket order (each lane reads back only
+    // its own slots of the list, written before the warp's last
+    // synchronisation); near-field records in plain order
+    const bool ordered = a.ratio != nullptr;
+    if (ordered) tile_order<ITEMS>(a, smem, begin, end, mat, slot, lane, list, hist);
 #pragma unroll 1
     for (int j = 0; j < ITEMS; ++j) {
-      const uint32_t e = list[j * 32 + lane];
+      uint32_t e = (uint32_t)(j * 32 + lane);
+      if (ordered) {
+        e = list[j * 32 + lane];
+      } else if (begin + e >= end) {
+        e = 0xffffffffu;
+      }
       if (e == 0xffffffffu) continue;
       const int64_t i = begin + (e & 0xffu);
       Record q;

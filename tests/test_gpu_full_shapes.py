@@ -1,0 +1,123 @@
+"""The batched and differentiable workloads at their full shapes.
+
+* 256 yarn materials with Zipf(1.1) record counts totalling 2^26 records,
+  material-sorted, run through the launch the benchmark times: the shape
+  picked by the library's autotuner, the fused op captured in a CUDA graph
+  and replayed; 3000 records sampled over the whole batch are checked
+  against the FP64 oracle with the parity rule (eval and sample).
+* The backward over 2^20 material-sorted records of the 64 fitting
+  materials, at the workload's full longitudinal range (v up to 100, where
+  the helix angles' gradients are largest), in the deterministic fixed-order
+  mode, against the oracle's exact gradient: per material and parameter
+  within 1e-4 of sum |g df/dtheta| (+1e-6), the float32 accumulation of
+  ~16k terms per material included.
+"""
+import numpy as np
+import pytest
+
+from oracle import parity as PU
+from paper_2401_12724_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2401_12724_gb300 import api as A
+    return A
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def test_batched_256_materials_full_size_graph_replay(orc, api):
+    from paper_2401_12724_gb300 import _native as N
+    mats = I.materials(4)
+    rec = I.records(4)
+    seg = I.seg_offsets(4)
+    n = rec["h"].shape[0]
+    assert n == 1 << 26 and seg[-1] == n
+    M = api.Materials(mats)
+    d = api.records_to_device(rec, "cuda", seg)
+    idx = I.sample_indices(4, 3000)
+    sub = {k: v[..., idx].copy() for k, v in rec.items()}
+    del rec
+    o = api.alloc_fused(n, "cuda")
+    tuned = api.autotune(M, N.OP_FUSED, d, out=o)
+    assert tuned["block"] in (128, 256, 512)
+    for t in o.values():
+        t.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        api.eval_sample_pdf(M, d, out=o, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        api.eval_sample_pdf(M, d, out=o)
+    for t in o.values():
+        t.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert M.workspace_error() == 0
+    got = {k: np_(v[..., idx]) for k, v in o.items()}
+    st_all = np_(o["status"])
+    assert set(np.unique(st_all)) <= {0, 1, 2, 3}
+    del d, o
+    torch.cuda.empty_cache()
+    ev = PU.oracle_view(orc, lambda r: orc.eval_records(mats, r, threads=8), mats, sub)
+    PU.assert_status(got["status"], ev, "c4full.status")
+    PU.assert_parity(got["f"], ev, 0, "c4full.f", gpu_status=got["status"])
+    PU.assert_parity(got["pdf"], ev, 1, "c4full.pdf", gpu_status=got["status"])
+
+    def code(r):
+        wo, w, p, st, lb = orc.sample_records(mats, r, threads=8)
+        return wo, w, p, st | (lb << 4)
+    sv = PU.oracle_view(orc, code, mats, sub, sample=True, values=(1, 2), status_idx=3,
+                        angle_idx=0)
+    ls = got["lobe_status"]
+    PU.assert_status(ls, sv, "c4full.lobe_status")
+    both = ((sv.base[3] & 15) == 0) & ((ls & 15) == 0)
+    with np.errstate(invalid="ignore"):
+        ang = np.where(both, PU.angle_between(got["wo"], sv.base[0]), 0.0)
+    PU.assert_parity(got["wo"], sv, 0, "c4full.wo", err=ang / PU.ANGLE, gpu_status=ls,
+                     direction=True)
+    PU.assert_parity(got["weight"], sv, 1, "c4full.weight", gpu_status=ls)
+    PU.assert_parity(got["pdf_s"], sv, 2, "c4full.pdf_s", gpu_status=ls)
+    M.close()
+
+
+def test_backward_2e20_records_64_materials_full_range(orc, api):
+    mats = I.materials(5)
+    n = 1 << 20
+    rec = I.random_records(n, n_mat=64, seed=501, wi_mode="cosine", sorted_ids=True, v_max=100.0)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 64)
+    g = np.random.default_rng(502).uniform(-1, 1, (3, n)).astype(np.float32)
+    # records without a derivative the float32 path can follow carry no weight
+    view = PU.oracle_view(orc, lambda r: orc.eval_records(mats, r, threads=16), mats, rec,
+                          n_random=0)
+    g[:, ~view.stable] = 0.0
+    grad_o, _, J = orc.grad_records(mats, rec, g.astype(np.float64), threads=16, jac=True)
+    scale = np.zeros((64, 8))
+    np.add.at(scale, rec["mat_id"], np.abs(g.T[:, :, None] * J).sum(1))
+    M = api.Materials(mats)
+    d = api.records_to_device(rec, "cuda", seg)
+    gt = torch.from_numpy(g).cuda()
+    a = np_(api.eval_backward(M, d, gt, deterministic=True))
+    b = np_(api.eval_backward(M, d, gt, deterministic=True))
+    assert np.array_equal(a, b)
+    err = np.abs(a - grad_o)
+    ratio = err / (1e-4 * scale + 1e-6)
+    assert (ratio <= 1.0).all(), (ratio.max(axis=0), np.unravel_index(ratio.argmax(), ratio.shape))
+    # the atomic mode agrees within the same bound
+    c = np_(api.eval_backward(M, d, gt))
+    assert (np.abs(c - grad_o) <= 1e-4 * scale + 1e-6).all()
+    # the helix angles' gradients at this range are large and still checked
+    assert np.abs(grad_o[:, 5:7]).max() > 100 * np.abs(grad_o[:, 0:3]).max()
+    M.close()

@@ -495,6 +495,46 @@ def test_autograd_function_and_fitting(orc, api):
     torch.testing.assert_close(th.grad, direct, rtol=0, atol=0)
 
 
+def test_fitting_the_ply_helix_angle(orc, api):
+    """Seven parameters fitted to oracle targets, the ply helix angle alpha_p
+    included.  The helix angles move the ply and fiber phases in proportion
+    to v, so the loss oscillates in them: the ply phase by
+    v (1 + tan^2 alpha_p) / (2 pi R_c) turns per radian, the fiber phase by
+    M v (1 + tan^2 alpha_f) / (2 pi R_fc) fiber periods per radian -- about
+    30 per radian at v = 2.  Over a short stretch of yarn (v < 2), from a
+    start 4% off, alpha_p lies in the basin of its true value; alpha_f, whose
+    loss repeats every few hundredths of a radian, stays at its value (its
+    gradient is checked against the oracle's in the backward tests)."""
+    mats = I.materials(5)[:4]
+    n = 4096
+    rec = I.random_records(n, n_mat=4, seed=65, wi_mode="cosine", sorted_ids=True, v_max=2.0)
+    seg = I.seg_offsets_from_ids(rec["mat_id"], 4)
+    M = api.Materials(mats)
+    d = dev(api, rec, seg)
+    theta_star = api.default_params(mats).cuda()
+    tgt, _, st_t = orc.eval_records(mats, rec, threads=8)
+    target = torch.from_numpy(tgt.astype(np.float32)).cuda()
+    mask = torch.from_numpy(st_t == 0).cuda()
+    free = [0, 1, 2, 3, 4, 5, 7]
+    g = torch.Generator().manual_seed(66)
+    start = theta_star.cpu()[:, free] * (1 + 0.04 * (2 * torch.rand(4, 7, generator=g) - 1))
+    x = start.cuda().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=0.002)
+    losses = []
+    for _ in range(200):
+        opt.zero_grad()
+        theta = torch.cat([x[:, :6], theta_star[:, 6:7], x[:, 6:7]], dim=1)
+        f, st = api.bysdf(theta, M, d)
+        loss = (((f - target) ** 2) * mask).sum() / n
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert losses[-1] < 0.15 * losses[0], losses[::20]
+    e0 = (start.cuda()[:, 5] - theta_star[:, 5]).abs().mean()
+    e1 = (x.detach()[:, 5] - theta_star[:, 5]).abs().mean()
+    assert e1 < 0.75 * e0, (float(e0), float(e1))
+
+
 def test_edge_cases(orc, api):
     mats = [I.material(n_plies=3)]
     M = api.Materials(mats)

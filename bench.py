@@ -380,9 +380,10 @@ def main():
     ap.add_argument("--records", type=int, default=0,
                     help="use only the first N records of the workload (profiling)")
     ap.add_argument("--profile-op", default="fused",
-                    choices=["fused", "backward", "trace", "multiscale"],
+                    choices=["fused", "backward", "l2", "trace", "multiscale"],
                     help="with --profile: fused = eval + sample + pdf over workload 2; "
-                         "backward = forward eval + backward over workload 5; trace = "
+                         "backward = forward eval + backward over workload 5; l2 = forward, "
+                         "L2 loss and backward in one pass over workload 5; trace = "
                          "2048 x 2048 camera rays against a 512-piece yarn patch; "
                          "multiscale = eval + sample + pdf over workload 3")
     args = ap.parse_args()
@@ -402,8 +403,8 @@ def main():
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
 
-    if args.profile and args.profile_op == "backward":
-        profile_backward(api, torch, args, rank)
+    if args.profile and args.profile_op in ("backward", "l2"):
+        profile_backward(api, torch, args, rank, l2=args.profile_op == "l2")
         return
     if args.profile and args.profile_op == "multiscale":
         M = api.Materials(I.materials(3))
@@ -539,8 +540,13 @@ def main():
             api.plain(N.OP_SAMPLE, M, ds, seg, out=plain_out)
             api.plain(N.OP_PDF, M, ds, seg, out=plain_out)
         ms_plain, _ = timed(plain_step, max(3, args.steps // 2), 2)
-        # like for like: the fused op in the plain per-material form
+        # like for like: the fused op in the plain per-material form, and the
+        # persistent kernel on the same material-sorted records
         ms_plain_fused, _ = timed(lambda: api.plain_fused(M, ds, seg, out=po),
+                                  max(3, args.steps // 2), 2)
+        dss = dict(ds)
+        dss["seg_offsets"] = torch.from_numpy(seg).cuda()
+        ms_pers_sorted, _ = timed(lambda: api.eval_sample_pdf(M, dss, out=po),
                                   max(3, args.steps // 2), 2)
         # the same three ops as separate persistent calls (no fusion)
         sep = lambda: (api.eval(M, d, out=out), api.sample(M, d, out=dict(  # noqa: E731
@@ -549,11 +555,16 @@ def main():
         ms_sep, _ = timed(sep, max(3, args.steps // 2), 2)
         line["vs_plain"] = dict(plain_fused_records_per_s=n / (ms_plain_fused / 1e3),
                                 fused_speedup_vs_plain_fused=ms_plain_fused / ms_step,
+                                note="the plain form needs its records sorted by material "
+                                     "(done outside its timed region); the timed step takes "
+                                     "them in any order",
+                                persistent_on_sorted_records_per_s=n / (ms_pers_sorted / 1e3),
+                                persistent_vs_plain_same_sorted_input=ms_plain_fused / ms_pers_sorted,
                                 plain_fused_launches_per_step=len(mats),
                                 plain_three_ops_records_per_s=n / (ms_plain / 1e3),
                                 separate_persistent_records_per_s=n / (ms_sep / 1e3),
                                 fused_speedup_vs_plain_three_ops=ms_plain / ms_step)
-        del ds, po, plain_out
+        del ds, dss, po, plain_out
         # the timed steps' outputs on the records the oracle checks
         m = min(CHECK_RECORDS, n)
         gpu_check = {k: (v[..., :m].cpu().numpy()) for k, v in out.items()}
@@ -568,9 +579,10 @@ def main():
     print(json.dumps(line), flush=True)
 
 
-def profile_backward(api, torch, args, rank):
+def profile_backward(api, torch, args, rank, l2=False):
     """Forward eval + backward steps over workload 5 (or its first --records
-    records), for a profiler; prints the mean step time."""
+    records), or (l2) the one-pass forward, L2 loss and backward, for a
+    profiler; prints the mean step time."""
     M = api.Materials(I.materials(5))
     rec, d, _ = workload_device(api, 5, rank, args.records)
     n = int(d["h"].shape[0])
@@ -578,13 +590,17 @@ def profile_backward(api, torch, args, rank):
     f = torch.empty(3, n, device="cuda")
     st = torch.empty(n, dtype=torch.uint8, device="cuda")
     gp = torch.empty(M.n_mat, 8, device="cuda")
+    target = (gf.abs() * 0.05).contiguous()
 
     def step():
+        if l2:
+            api.eval_l2_backward(M, d, target)
+            return
         api.eval(M, d, with_pdf=False, out=dict(f=f, status=st))
         api.eval_backward(M, d, gf, out=gp)
     ms, _ = timed(step, args.steps, args.warmup)
-    print(json.dumps(dict(profile="backward", workload=I.WORKLOAD_NAME[5], records=n,
-                          ms_per_step=ms)), flush=True)
+    print(json.dumps(dict(profile="l2" if l2 else "backward", workload=I.WORKLOAD_NAME[5],
+                          records=n, ms_per_step=ms)), flush=True)
 
 
 def other_workloads(api, N, torch, args, sm_count):
@@ -598,8 +614,27 @@ def other_workloads(api, N, torch, args, sm_count):
     o = dict(f=torch.empty(3, n, device="cuda"), pdf=torch.empty(n, device="cuda"),
              status=torch.empty(n, dtype=torch.uint8, device="cuda"))
     ms, _ = timed(lambda: api.eval(M, d, out=o), steps * 4, 3)
+    # the same calls replayed from a CUDA graph (16 calls per graph): the
+    # device time per call without the Python binding's per-call host cost
+    calls = 16
+    g1 = torch.cuda.CUDAGraph()
+    s1 = torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s1):
+        api.eval(M, d, out=o, stream=s1)
+    torch.cuda.current_stream().wait_stream(s1)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g1):
+        for _ in range(calls):
+            api.eval(M, d, out=o)
+    ms_g, _ = timed(g1.replay, steps, 3)
+    ms_g /= calls
     res[I.WORKLOAD_NAME[1]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
-                                   roofline_frac=frac(OPS[1]["eval"], n, ms, sm_count))
+                                   roofline_frac=frac(OPS[1]["eval"], n, ms, sm_count),
+                                   graph_ms_per_call=ms_g,
+                                   graph_records_per_s=n / (ms_g / 1e3),
+                                   graph_roofline_frac=frac(OPS[1]["eval"], n, ms_g, sm_count))
+    del g1
     # multi-scale: fused eval + sample
     mats = I.materials(3)
     M = api.Materials(mats)
@@ -711,13 +746,32 @@ def other_workloads(api, N, torch, args, sm_count):
     ms_f, _ = timed(lambda: api.eval(M, d, with_pdf=False, out=dict(f=f, status=st)), steps, 2)
     ms_b, _ = timed(lambda: api.eval_backward(M, d, gf, out=gp), max(3, steps // 2), 1)
     fwd_bwd_ops = tuple(a + b for a, b in zip(OPS[5]["eval"], OPS[5]["backward"]))
+    # the fitting step of the workload: forward, L2 loss against target
+    # radiance and its gradient in one pass (bysdf_eval_l2_backward), the
+    # forward values written; the target is the forward at held-out
+    # parameters (20% off), evaluated once outside the timed region
+    theta = api.default_params(mats).cuda()
+    held = theta * (1 + 0.2 * (2 * torch.rand(theta.shape, generator=torch.Generator().manual_seed(5))
+                                .cuda() - 1))
+    M.set_params(held)
+    target = api.eval(M, d, with_pdf=False)[0].clone()
+    M.set_params(theta)
+    ms_l2, _ = timed(lambda: api.eval_l2_backward(M, d, target), max(3, steps // 2), 1)
+    # its work: the backward's count already holds one forward evaluation;
+    # the loss adds 9 flops per record
+    l2_ops = (OPS[5]["backward"][0] + 9.0, OPS[5]["backward"][1])
     # the extended parameter set (15 columns), and with the per-record
     # direction products
     ms_x, _ = timed(lambda: api.eval_backward_ext(M, d, gf), max(3, steps // 4), 1)
     ms_xd, _ = timed(lambda: api.eval_backward_ext(M, d, gf, dirs=True), max(3, steps // 8), 1)
-    res[I.WORKLOAD_NAME[5]] = dict(records_per_s=n / (ms_fb / 1e3), ms=ms_fb, records=n,
-                                   roofline_frac=frac(fwd_bwd_ops, n, ms_fb, sm_count),
-                                   roofline_pipe=pipe_of(fwd_bwd_ops, n, ms_fb, sm_count),
+    res[I.WORKLOAD_NAME[5]] = dict(records_per_s=n / (ms_l2 / 1e3), ms=ms_l2, records=n,
+                                   step="forward + L2 loss + backward in one pass",
+                                   roofline_frac=frac(l2_ops, n, ms_l2, sm_count),
+                                   roofline_pipe=pipe_of(l2_ops, n, ms_l2, sm_count),
+                                   two_calls_records_per_s=n / (ms_fb / 1e3),
+                                   two_calls_step="eval, then backward of a given "
+                                                  "upstream gradient",
+                                   two_calls_roofline_frac=frac(fwd_bwd_ops, n, ms_fb, sm_count),
                                    forward_only_records_per_s=n / (ms_f / 1e3),
                                    roofline_frac_forward=frac(OPS[5]["eval"], n, ms_f, sm_count),
                                    backward_only_records_per_s=n / (ms_b / 1e3),

@@ -28,7 +28,9 @@
  * buffer must be 16-byte aligned.  Calls are asynchronous on `stream`
  * (a cudaStream_t; NULL = legacy default stream) and allocate no memory: the
  * caller provides a workspace of at least bysdf_workspace_size() bytes, which
- * must not be shared by calls that may run concurrently.
+ * must not be shared by calls that may run concurrently.  Its contents need
+ * no initialisation: each launch claims the workspace's control words for
+ * itself (they carry the launch's epoch) before it uses them.
  *
  * Per-record status (uint8): 0 ok; 1 no ply hit (the ray passes through the
  * yarn, f = 0, pdf = 0); 2 invalid input (non-finite value, |h| > 1, a
@@ -377,6 +379,24 @@ typedef struct bysdf_outputs {
   uint8_t* lobe_status;  /* sample                                          */
   float* grad_params;    /* backward: [n_mat][8]                            */
 } bysdf_outputs;
+
+/* Forward, L2 loss and its parameter gradient in one pass (the fitting of
+ * Sec. 5.2 as a loss against target radiance; the backward of
+ * bysdf_eval_backward with the upstream gradient 2 w (f - target) formed
+ * from each record's own f, so the forward is not run twice):
+ *   loss_mat[k] = sum over the records of material k with status 0 of
+ *                 w_i sum_c (f_c(i) - target_c(i))^2,
+ *   grad_params = d (sum_k loss_mat[k]) / d params, [n_mat][8] as in
+ *                 bysdf_eval_backward (written by the callee).
+ * target_rgb: 3 planes, required; weight: per-record w_i, NULL = 1; f_rgb
+ * (nullable): the forward values, 0 where a record has no valid
+ * evaluation; loss_mat (nullable, 4-byte aligned): [n_mat].  Deterministic
+ * mode as bysdf_eval_backward.  Errors as bysdf_eval_backward; a NULL target
+ * with n > 0: BYSDF_E_ARG. */
+int bysdf_eval_l2_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                           const float* target_rgb, const float* weight, float* f_rgb,
+                           float* loss_mat, float* grad_params, int deterministic,
+                           void* workspace, size_t workspace_bytes, void* stream);
 
 /* The plain per-material form of the fused op (bysdf_eval_sample_pdf): one
  * launch per material over its sorted record range, one thread per record,

@@ -151,6 +151,7 @@ enum {
   MG_LOBE,        // lobe choice by u0 (Sec. 4.1.5)
   MG_SAMPLE,      // validity of the sampled direction, sampler frame
   MG_SHADOW,      // ply shadowing: shadow ray vs another ply's circle (Sec. 4.1.4)
+  MG_KINK,        // fiber maps: distance to a texel centre, where the slope changes
   MG_N = 10
 };
 thread_local double* g_mg = nullptr;
@@ -528,6 +529,9 @@ void fiber_lookup_tab(const MatStatic& st, int Mk, const std::vector<double>& ta
   {
     const double tv = val(tau);
     mg(MG_CUSP, (tv < 0.0 || tv >= T - 1.0) ? 0.0 : std::min(tv, (T - 1.0) - tv) / T);
+    // the interpolant's slope changes at every texel centre: the value is
+    // continuous there, its derivatives are not
+    mg(MG_KINK, (tv - std::floor(tv + 0.5)) / T);
   }
   const S f = tau - fl;
   const int i0 = (((int)fl) % T + T) % T;

@@ -142,6 +142,8 @@ int orc_sample_stochastic(const orc_material* m, int n_mat, const orc_records* r
  *   6 lobe choice: u0 against the cumulative lobe probabilities
  *   7 sampled direction: side tests, the sampler's disk frame
  *   8 ply shadowing: the shadow ray grazing another ply's circle
+ *   9 fiber maps: distance in fiber periods to the nearest texel centre, where
+ *     the interpolant's slope (and so every derivative) changes
  * out: [n][ORC_MG_N], the smallest distance per class (+inf where a record
  * never reaches the class; the row stays +inf for invalid records). */
 #define ORC_MG_N 10

@@ -329,7 +329,8 @@ def sample_stochastic_records(mats, rec, seed: int, flags: int, index_offset: in
 
 
 MG_N = 10
-MARGIN_CLASSES = ("graze", "gap", "cusp", "axis", "hemi", "exit", "lobe", "sample", "shadow")
+MARGIN_CLASSES = ("graze", "gap", "cusp", "axis", "hemi", "exit", "lobe", "sample", "shadow",
+                  "kink")
 
 
 def margins(mats, rec, op: str = "eval", seed: int = 0, flags: int = 0, index_offset: int = 0,

@@ -292,10 +292,65 @@ def assert_status(gpu_st, view: Oracle, name: str, code=None):
     return float((gpu_st == base).mean())
 
 
-def stable_mask(view: Oracle):
-    """Records with a unique derivative for the gradient tests: the
-    well-conditioned ones."""
-    return view.stable
+KINK = 1e-5          # fiber periods: a few times the float32 path's phase error
+JAC_STABLE = 1e-3    # relative change of a record's Jacobian under one internal move
+
+
+def gradient_spread(orc, mats, rec, view: Oracle, **margin_kw):
+    """(mask, dJ) for the gradient tests.
+
+    mask: records whose derivatives the float32 path can follow --
+    well-conditioned; no fiber-map lookup within KINK periods of a texel
+    centre (the interpolant's slope changes there, and the helix angles'
+    derivatives carry that slope times hundreds of periods per radian); and
+    a Jacobian (oracle, 8 parameters) that moves by at most JAC_STABLE of
+    itself when the azimuth u, the hit distance or the ply azimuth moves by
+    about one float32 rounding.
+
+    dJ [n, 3, 8]: the largest change of each Jacobian entry under those
+    moves -- how far a float32 evaluation of the derivative may honestly sit
+    from the exact one.  At large |v| the helix angles' derivatives are
+    products of the phase v tan(alpha) with slopes that vary over a fraction
+    of a fiber period, so dJ reaches a few 1e-4 of J there."""
+    mg = orc.margins(mats, rec, "eval", threads=8, **margin_kw)
+    good = view.stable & (mg[orc.MARGIN_CLASSES.index("kink")] >= KINK)
+    n = good.shape[0]
+    g = np.ones((3, n))
+    _, _, J0 = orc.grad_records(mats, rec, g, threads=8, jac=True)
+    size = np.abs(J0).max(axis=1)                      # [n, 8]
+    dJ = np.zeros_like(J0)
+
+    def moved(J1):
+        nonlocal dJ
+        dJ = np.maximum(dJ, np.abs(J1 - J0))
+
+    for kw in (dict(dt=SIGMA), dict(dt=-SIGMA), dict(du_ply=UPLY), dict(du_ply=-UPLY)):
+        with orc.internal_offsets(**kw):
+            moved(orc.grad_records(mats, rec, g, threads=8, jac=True)[2])
+    for s in (-SIGMA, SIGMA):
+        r = dict(rec)
+        r["u"] = (rec["u"].astype(np.float64) + s).astype(np.float32)
+        moved(orc.grad_records(mats, r, g, threads=8, jac=True)[2])
+    rel = np.where(size > 0, dJ.max(axis=1) / (size + 1e-12), 0.0).max(axis=1)
+    return good & (rel <= JAC_STABLE), dJ
+
+
+def gradient_mask(orc, mats, rec, view: Oracle, **margin_kw):
+    """The mask of gradient_spread alone."""
+    return gradient_spread(orc, mats, rec, view, **margin_kw)[0]
+
+
+def gradient_bound(mat_id, g, J, dJ, n_mat: int, rel: float = 1e-4, abs_: float = 1e-6):
+    """Per-material tolerance [n_mat, 8] of a float32 gradient
+    sum_records sum_c g_c dJ_c/dtheta: rel of sum |g J| (the float32
+    accumulation and arithmetic) plus sum |g| dJ (each record's Jacobian
+    known only to within its spread under float32 rounding of its inputs)
+    plus abs_."""
+    g = np.asarray(g, np.float64)
+    t = rel * np.abs(g.T[:, :, None] * J).sum(1) + (np.abs(g.T)[:, :, None] * dJ).sum(1)
+    out = np.zeros((n_mat, J.shape[2]))
+    np.add.at(out, mat_id, t)
+    return out + abs_
 
 
 def dump(name: str, **arrays):

@@ -83,6 +83,8 @@ SYMBOLS = [
     ("bysdf_eval_backward_ext", C.c_int,
      [P, C.POINTER(Hits), C.c_int64, P, P, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_plain", C.c_int, [C.c_int, P, C.POINTER(Hits), P, P, P, C.c_int64, P, P, P, P, P, P]),
+    ("bysdf_eval_l2_backward", C.c_int,
+     [P, C.POINTER(Hits), C.c_int64, P, P, P, P, P, C.c_int, P, C.c_size_t, P]),
     ("bysdf_plain_fused", C.c_int,
      [P, C.POINTER(Hits), P, P, P, C.c_int64, C.POINTER(Outputs), P]),
     ("bysdf_set_launch_config", C.c_int, [P, C.c_int, C.POINTER(LaunchConfig)]),

@@ -320,6 +320,25 @@ def eval_backward(mats: Materials, rec: dict, grad_f: torch.Tensor, deterministi
     return g
 
 
+def eval_l2_backward(mats: Materials, rec: dict, target: torch.Tensor, weight=None,
+                     deterministic: bool = False, stream=None, with_f: bool = True):
+    """Forward, L2 loss against target (3, n) and its parameter gradient in
+    one pass (bysdf_eval_l2_backward): returns grad (n_mat, 8), per-material
+    loss (n_mat,) and f (3, n) (None unless with_f)."""
+    n = _n(rec)
+    dev = rec["h"].device
+    g = _empty((mats.n_mat, 8), torch.float32, dev)
+    loss = _empty((mats.n_mat,), torch.float32, dev)
+    f = _empty((3, n), torch.float32, dev) if with_f else None
+    t = target.contiguous()
+    w = None if weight is None else weight.contiguous()
+    ws = mats.workspace(n)
+    N.check(mats.lib.bysdf_eval_l2_backward(
+        mats.handle, C.byref(hits_struct(rec)), n, _ptr(t), _ptr(w), _ptr(f), _ptr(loss), _ptr(g),
+        int(deterministic), _ptr(ws), ws.numel(), _stream(stream)), "bysdf_eval_l2_backward")
+    return g, loss, f
+
+
 def eval_backward_ext(mats: Materials, rec: dict, grad_f: torch.Tensor,
                       deterministic: bool = False, dirs: bool = False, stream=None):
     """d(sum grad_f * f) / d params for the 15-column extended set, and with
@@ -431,6 +450,31 @@ class BYSDFEval(torch.autograd.Function):
 def bysdf(params: torch.Tensor, mats: Materials, rec: dict, deterministic: bool = False):
     """Differentiable evaluation: returns f (3, n) and status (n,)."""
     return BYSDFEval.apply(params, mats, rec, deterministic)
+
+
+class BYSDFL2Loss(torch.autograd.Function):
+    """loss = sum_i w_i sum_c (f_c(i) - target_c(i))^2 over the records with
+    status 0, differentiable in the 8 parameters; forward and backward are
+    one library pass (bysdf_eval_l2_backward), whose gradient is kept for
+    backward."""
+
+    @staticmethod
+    def forward(ctx, params, mats, rec, target, weight=None, deterministic=False):
+        mats.set_params(params)
+        g, loss, _ = eval_l2_backward(mats, rec, target, weight, deterministic, with_f=False)
+        ctx.save_for_backward(g)
+        return loss.sum()
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (g,) = ctx.saved_tensors
+        return g * grad_loss, None, None, None, None, None
+
+
+def bysdf_l2_loss(params: torch.Tensor, mats: Materials, rec: dict, target: torch.Tensor,
+                  weight=None, deterministic: bool = False) -> torch.Tensor:
+    """Differentiable L2 loss of the BYSDF against target radiance (scalar)."""
+    return BYSDFL2Loss.apply(params, mats, rec, target, weight, deterministic)
 
 
 class BYSDFEvalExt(torch.autograd.Function):

@@ -3,6 +3,7 @@
 // 1D fiber maps, computed in double on the host), workspace planning, kernel
 // dispatch, the plain per-material form and the launch-shape autotuner.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -295,11 +296,12 @@ __global__ void k_read_params(const uint8_t* table, int n_mat, int stride, float
   for (int k = 0; k < ncol; ++k) params[(size_t)i * ncol + k] = (float)p[k];
 }
 
-// Tile plan: reset the tile counter and the error word; for material-sorted
-// records also the first warp tile of every material (exclusive scan of
-// ceil(count / tile)).
+// Tile plan: set the control words for the launch's epoch (tile draws
+// counted from 0, no error); for material-sorted records also the first
+// warp tile of every material (exclusive scan of ceil(count / tile)).
 __global__ void __launch_bounds__(1024) k_plan(WsCtl* ctl, int32_t* tile_start,
-                                               const int64_t* seg, int n_mat, int tile) {
+                                               const int64_t* seg, int n_mat, int tile,
+                                               unsigned long long epoch) {
   __shared__ int64_t part[1024];
   const int tid = threadIdx.x;
   if (seg != nullptr) {
@@ -327,12 +329,17 @@ __global__ void __launch_bounds__(1024) k_plan(WsCtl* ctl, int32_t* tile_start,
     if (tid == 1023) tile_start[n_mat] = (int32_t)part[1023];
   }
   if (tid == 0) {
-    ctl->tile_counter = 0;
-    ctl->err = 0u;
+    ctl->tile_word = 0ull;
+    ctl->err_word = epoch << kEpochShift;
   }
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bytes between two materials' tables when all of them sit in shared
+// memory: the table stride plus 16, so that successive tables start four
+// banks apart.
+size_t smem_stride(const bysdf_materials* m) { return (size_t)m->stride + 16; }
 size_t ws_tile_start_off() { return kWsCtl; }
 size_t ws_partials_off(int n_mat) { return align_up(kWsCtl + 4 * (size_t)(n_mat + 1), 256); }
 int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
@@ -398,6 +405,7 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
   a->table = m->d_table;
   a->n_mat = m->n_mat;
   a->stride = m->stride;
+  a->sstride = smem_stride(m);
   a->n = n;
   a->tile = 32 * items;
   a->h = h->h;
@@ -410,7 +418,7 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
   a->seg = h->seg_offsets;
   if (h->seg_offsets) {
     a->mode = MODE_SORTED;
-  } else if ((size_t)m->n_mat * m->stride <= kAllSmemMax) {
+  } else if ((size_t)m->n_mat * smem_stride(m) <= kAllSmemMax) {
     a->mode = MODE_ALL_SMEM;
   } else {
     return fail(BYSDF_E_UNSUPPORTED,
@@ -429,9 +437,30 @@ int prepare(const bysdf_materials* m, const bysdf_hits* h, int64_t n, void* ws, 
   return BYSDF_OK;
 }
 
-int plan(const bysdf_materials* m, KArgs& a, void* ws, cudaStream_t st) {
+// A new epoch for every launch that uses a workspace's control words: 40
+// bits, never 0, increasing through the process (it wraps after 2^40
+// launches).
+uint64_t next_epoch() {
+  static std::atomic<uint64_t> counter{0};
+  for (;;) {
+    const uint64_t e = (counter.fetch_add(1, std::memory_order_relaxed) + 1) &
+                       ((1ull << (64 - kEpochShift)) - 1);
+    if (e) return e;
+  }
+}
+
+// Gives the launch its epoch.  Records in any order, with fewer than 2^24
+// tile draws (tiles plus one final draw per warp): the launch claims the
+// control words itself and nothing else is launched.  Otherwise k_plan runs
+// first (for material-sorted records it also computes the first tile of
+// every material).
+int plan(const bysdf_materials* m, KArgs& a, void* ws, cudaStream_t st, int64_t grid_warps) {
+  a.epoch = next_epoch();
+  a.claim_tiles = a.mode != MODE_SORTED && a.n_tiles + grid_warps < (1ll << kEpochShift);
+  if (a.claim_tiles) return BYSDF_OK;
   k_plan<<<1, 1024, 0, st>>>(a.ctl, reinterpret_cast<int32_t*>((uint8_t*)ws + ws_tile_start_off()),
-                             a.mode == MODE_SORTED ? a.seg : nullptr, m->n_mat, a.tile);
+                             a.mode == MODE_SORTED ? a.seg : nullptr, m->n_mat, a.tile,
+                             (unsigned long long)a.epoch);
   BY_CU(cudaGetLastError());
   return BYSDF_OK;
 }
@@ -518,7 +547,7 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
   }
   // tables, then each warp's tile order list (4 bytes per record of a tile)
   // and bucket counts
-  const size_t tables = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
+  const size_t tables = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * a.sstride
                                                 : (size_t)(c.block / 32) * m->stride;
   a.order_off = (int32_t)align_up(tables, 16);
   auto key_bytes = [&](int items) {
@@ -540,8 +569,9 @@ int run_forward(const bysdf_materials* m, int op, const bysdf_hits* h, const flo
     if (smem > 48 * 1024) BY_CU(set_forward_smem_limit(bits, c.block, 1, c.occupancy, smem));
     BY_CU(cached_forward_occupancy(m, bits, c.block, 1, c.occupancy, smem, &occ));
   }
-  if ((rc = plan(m, a, ws, st))) return rc;
-  BY_CU(launch_forward(bits, a, c.block, c.occupancy, grid_for(m, c, occ), smem, st));
+  const int grid = grid_for(m, c, occ);
+  if ((rc = plan(m, a, ws, st, (int64_t)grid * (c.block / 32)))) return rc;
+  BY_CU(launch_forward(bits, a, c.block, c.occupancy, grid, smem, st));
   return BYSDF_OK;
 }
 
@@ -565,23 +595,43 @@ int get_params(const bysdf_materials* m, float* params, int ncol, void* stream) 
   return BYSDF_OK;
 }
 
-// ext: 15 gradient columns (else 8); grad_wi / grad_wo: direction
+// kind: KB_BASIC (8 gradient columns), KB_EXT (15) or KB_L2 (8, upstream
+// gradient of the L2 loss against l2->target); grad_wi / grad_wo: direction
 // vector-Jacobian products (extended call only), each optional.
+struct L2Args {
+  const float* target;
+  const float* weight;
+  float* f_rgb;
+  float* loss_mat;
+};
 int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const float* grad_f,
                  float* grad_params, int deterministic, void* ws, size_t ws_bytes,
-                 cudaStream_t st, const bysdf_launch_config& c, bool ext = false,
-                 float* grad_wi = nullptr, float* grad_wo = nullptr) {
-  const int np = ext ? BYSDF_NPARAM_EXT : BYSDF_NPARAM;
+                 cudaStream_t st, const bysdf_launch_config& c, int kind = KB_BASIC,
+                 float* grad_wi = nullptr, float* grad_wo = nullptr,
+                 const L2Args* l2 = nullptr) {
+  const bool ext = kind == KB_EXT;
+  const int ng = ext ? BYSDF_NPARAM_EXT : BYSDF_NPARAM;   // gradient columns
+  const int np = kind == KB_L2 ? ng + 1 : ng;             // accumulated columns
   int rc = check_hits(m, h, true, n);
   if (rc) return rc;
   if ((rc = check_out(grad_params, "grad_params"))) return rc;
-  if (n > 0 && (rc = check_out(grad_f, "grad_f"))) return rc;
+  if (kind == KB_L2) {
+    if (n > 0 && (rc = check_out(l2->target, "target"))) return rc;
+    if (l2->weight && !aligned16(l2->weight)) return fail(BYSDF_E_ARG, "weight not 16-byte aligned");
+    if (l2->f_rgb && !aligned16(l2->f_rgb)) return fail(BYSDF_E_ARG, "f_rgb not 16-byte aligned");
+    if (l2->loss_mat && ((uintptr_t)l2->loss_mat & 3u))
+      return fail(BYSDF_E_ARG, "loss_mat not 4-byte aligned");
+  } else if (n > 0 && (rc = check_out(grad_f, "grad_f"))) {
+    return rc;
+  }
   if (grad_wi && (rc = check_out(grad_wi, "grad_wi"))) return rc;
   if (grad_wo && (rc = check_out(grad_wo, "grad_wo"))) return rc;
   if (deterministic && !h->seg_offsets)
     return fail(BYSDF_E_UNSUPPORTED, "deterministic backward needs material-sorted records");
+  if (kind == KB_L2 && l2->loss_mat && (n == 0 || !deterministic))
+    BY_CU(cudaMemsetAsync(l2->loss_mat, 0, sizeof(float) * m->n_mat, st));
   if (n == 0) {
-    BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * np * m->n_mat, st));
+    BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * ng * m->n_mat, st));
     return BYSDF_OK;
   }
   KArgs a;
@@ -590,30 +640,38 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
   a.grad_f = grad_f;
   a.grad_params = grad_params;
   a.n_param = np;
+  if (kind == KB_L2) {
+    a.target = l2->target;
+    a.weight = l2->weight;
+    a.f_rgb = l2->f_rgb;
+    a.loss_mat = l2->loss_mat;
+  }
   a.partials = deterministic ? reinterpret_cast<float*>((uint8_t*)ws + ws_partials_off(m->n_mat))
                              : nullptr;
   const size_t smem = a.mode == MODE_ALL_SMEM
-                          ? (size_t)m->n_mat * m->stride + sizeof(float) * np * m->n_mat
+                          ? (size_t)m->n_mat * a.sstride + sizeof(float) * np * m->n_mat
                           : (size_t)(c.block / 32) * m->stride;
   if (smem > m->smem_optin) return fail(BYSDF_E_UNSUPPORTED, "material table too large for shared memory");
-  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, c.occupancy, ext, smem));
+  if (smem > 48 * 1024) BY_CU(set_backward_smem_limit(c.block, c.occupancy, kind, smem));
   int occ = 0;
-  BY_CU(backward_occupancy(c.block, c.occupancy, ext, smem, &occ));
-  if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * np * m->n_mat, st));
-  if ((rc = plan(m, a, ws, st))) return rc;
-  BY_CU(launch_backward(a, c.block, c.occupancy, ext, grid_for(m, c, occ), smem, st));
+  BY_CU(backward_occupancy(c.block, c.occupancy, kind, smem, &occ));
+  if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * ng * m->n_mat, st));
+  const int grid = grid_for(m, c, occ);
+  if ((rc = plan(m, a, ws, st, (int64_t)grid * (c.block / 32)))) return rc;
+  BY_CU(launch_backward(a, c.block, c.occupancy, kind, grid, smem, st));
   if (deterministic) BY_CU(launch_reduce_partials(a, st));
   if (grad_wi || grad_wo) {
     // second pass: the direction products (its own tile plan)
     a.grad_wi = grad_wi;
     a.grad_wo = grad_wo;
-    const size_t smem_d = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * m->stride
+    const size_t smem_d = a.mode == MODE_ALL_SMEM ? (size_t)m->n_mat * a.sstride
                                                   : (size_t)(c.block / 32) * m->stride;
     if (smem_d > 48 * 1024) BY_CU(set_dirgrad_smem_limit(c.block, smem_d));
     int occ_d = 0;
     BY_CU(dirgrad_occupancy(c.block, smem_d, &occ_d));
-    if ((rc = plan(m, a, ws, st))) return rc;
-    BY_CU(launch_dirgrad(a, c.block, grid_for(m, c, occ_d), smem_d, st));
+    const int grid_d = grid_for(m, c, occ_d);
+    if ((rc = plan(m, a, ws, st, (int64_t)grid_d * (c.block / 32)))) return rc;
+    BY_CU(launch_dirgrad(a, c.block, grid_d, smem_d, st));
   }
   return BYSDF_OK;
 }
@@ -839,9 +897,10 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
   void* scratch = nullptr;
   if ((rc = noalloc_scratch(&scratch))) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // the previous call's contents stay in the array; the tile plan that
-  // starts every forward launch sets the control words (tile counter, error
-  // word) to zero, and the per-material entries are rewritten by it
+  // the previous call's contents stay in the array: every launch claims
+  // the control words (tile draws, error word) for its own epoch, and the
+  // per-material entries of material-sorted records are rewritten by the
+  // tile plan launched before it
   bysdf_outputs o{};
   o.f_rgb = f_rgb;
   o.pdf = pdf;
@@ -904,7 +963,7 @@ int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with
                                bysdf_host_pipeline** out) {
   if (!m || !out) return fail(BYSDF_E_ARG, "NULL argument");
   if (chunk < 1024 || chunk > ((int64_t)1 << 28)) return fail(BYSDF_E_ARG, "chunk outside [1024, 2^28]");
-  if ((size_t)m->n_mat * m->stride > kAllSmemMax)
+  if ((size_t)m->n_mat * smem_stride(m) > kAllSmemMax)
     return fail(BYSDF_E_UNSUPPORTED, "host pipeline: tables must fit in shared memory");
   *out = nullptr;
   bysdf_host_pipeline* p = new bysdf_host_pipeline();
@@ -1199,7 +1258,18 @@ int bysdf_eval_backward_ext(const bysdf_materials* m, const bysdf_hits* hits, in
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   return run_backward(m, hits, n, grad_f, grad_params, deterministic, workspace,
                       workspace_bytes, reinterpret_cast<cudaStream_t>(stream),
-                      m->cfg[BYSDF_OP_BACKWARD], true, grad_wi, grad_wo);
+                      m->cfg[BYSDF_OP_BACKWARD], KB_EXT, grad_wi, grad_wo);
+}
+
+int bysdf_eval_l2_backward(const bysdf_materials* m, const bysdf_hits* hits, int64_t n,
+                           const float* target_rgb, const float* weight, float* f_rgb,
+                           float* loss_mat, float* grad_params, int deterministic,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+  if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
+  L2Args l2{target_rgb, weight, f_rgb, loss_mat};
+  return run_backward(m, hits, n, nullptr, grad_params, deterministic, workspace,
+                      workspace_bytes, reinterpret_cast<cudaStream_t>(stream),
+                      m->cfg[BYSDF_OP_BACKWARD], KB_L2, nullptr, nullptr, &l2);
 }
 
 int bysdf_plain(int op, const bysdf_materials* m, const bysdf_hits* hits,
@@ -1392,10 +1462,13 @@ int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls) {
 int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err) {
   if (!workspace || !err) return fail(BYSDF_E_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const uint8_t* p = reinterpret_cast<const uint8_t*>(workspace) + offsetof(WsCtl, err);
-  BY_CU(cudaMemcpyAsync(err, p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  // the word is epoch << 24 | error bits (the epoch of the last launch)
+  const uint8_t* p = reinterpret_cast<const uint8_t*>(workspace) + offsetof(WsCtl, err_word);
+  unsigned long long word = 0;
+  BY_CU(cudaMemcpyAsync(&word, p, sizeof(word), cudaMemcpyDeviceToHost, st));
   BY_CU(cudaStreamSynchronize(st));
-  BY_CU(cudaMemsetAsync(const_cast<uint8_t*>(p), 0, sizeof(uint32_t), st));
+  BY_CU(cudaMemsetAsync(const_cast<uint8_t*>(p), 0, sizeof(word), st));
+  *err = (uint32_t)(word & ((1ull << kEpochShift) - 1));
   return BYSDF_OK;
 }
 

@@ -5,7 +5,9 @@
 // parameters in closed form) and reduces sum_c g_c df_c/dtheta per material --
 // warp shuffles over a single-material warp tile, then one atomic (or one
 // fixed-order partial) per tile; with unsorted records, shared-memory
-// accumulators per CTA.  EXT selects the 15-column extended set.
+// accumulators per CTA.  KIND: the 8-column basic set, the 15-column
+// extended set, or the basic set with the upstream gradient of an L2 loss
+// (its value a ninth accumulated column, flushed to the per-material loss).
 //
 // k_dirgrad: per-record vector-Jacobian products with respect to the record's
 // directions, forward mode with 6 tangents (wi, wo); no reduction.
@@ -13,13 +15,14 @@
 
 namespace bysdf {
 
-template <int BLOCK, int MINB, bool EXT>
+template <int BLOCK, int MINB, int KIND>
 __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
-  constexpr int NP = EXT ? 15 : 8;
+  constexpr int NP = KbCols<KIND>::acc;      // accumulated columns
+  constexpr int NG = KbCols<KIND>::grad;     // gradient columns of grad_params
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[2 * (BLOCK / 32)];
   // MODE_ALL_SMEM: per-CTA accumulators behind the tables
-  float* sacc = reinterpret_cast<float*>(smem + (size_t)a.n_mat * a.stride);
+  float* sacc = reinterpret_cast<float*>(smem + (size_t)a.n_mat * a.sstride);
   if (a.mode == MODE_ALL_SMEM) {
     for (int k = threadIdx.x; k < a.n_mat * NP; k += BLOCK) sacc[k] = 0.f;
   }
@@ -43,11 +46,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
       } else {
         q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
-        tb = smem + (size_t)mm * a.stride;
+        tb = smem + (size_t)mm * a.sstride;
       }
       const MatDev* m = reinterpret_cast<const MatDev*>(tb);
       float g[NP];
-      backward_record<EXT>(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
+      backward_record<KIND>(a, *m, reinterpret_cast<const float2*>(m + 1), i, q, g);
       if (mat >= 0) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) acc[k] += g[k];
@@ -71,15 +74,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
           for (int k = 0; k < NP; ++k) a.partials[(size_t)tile * NP + k] = acc[k];
         } else {
 #pragma unroll
-          for (int k = 0; k < NP; ++k) atomicAdd(a.grad_params + (size_t)mat * NP + k, acc[k]);
+          for (int k = 0; k < NP; ++k) {
+            if (k < NG) atomicAdd(a.grad_params + (size_t)mat * NG + k, acc[k]);
+            else if (a.loss_mat) atomicAdd(a.loss_mat + mat, acc[k]);
+          }
         }
       }
     }
   });
   if (a.mode == MODE_ALL_SMEM) {
     __syncthreads();
-    for (int k = threadIdx.x; k < a.n_mat * NP; k += BLOCK)
-      if (sacc[k] != 0.f) atomicAdd(a.grad_params + k, sacc[k]);
+    for (int k = threadIdx.x; k < a.n_mat * NP; k += BLOCK) {
+      if (sacc[k] == 0.f) continue;
+      const int mm = k / NP, c = k - mm * NP;
+      if (c < NG) atomicAdd(a.grad_params + (size_t)mm * NG + c, sacc[k]);
+      else if (a.loss_mat) atomicAdd(a.loss_mat + mm, sacc[k]);
+    }
   }
 }
 
@@ -98,12 +108,15 @@ __global__ void k_reduce_partials(const KArgs a) {
     for (int k = 0; k < 16; ++k)
       if (k < np) acc[k] += a.partials[(size_t)t * np + k];
   }
+  // gradient columns to grad_params; the L2 backward's loss column to loss_mat
+  const int ng = a.target ? np - 1 : np;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     float v = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0 && k < np) a.grad_params[(size_t)m * np + k] = v;
+    if (lane == 0 && k < ng) a.grad_params[(size_t)m * ng + k] = v;
+    if (lane == 0 && k == ng && k < np && a.loss_mat) a.loss_mat[m] = v;
   }
 }
 
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
       } else {
         q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
-        tb = smem + (size_t)mm * a.stride;
+        tb = smem + (size_t)mm * a.sstride;
       }
       const MatDev* m = reinterpret_cast<const MatDev*>(tb);
       float gwi[3], gwo[3];
@@ -181,17 +194,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
 
 // occupancy 0: registers as needed (8 warps per SM at 256 threads);
 // occupancy 1: at most 128 registers (16 warps per SM; the rest spills).
-template <bool EXT>
+template <int KIND>
 static const void* bwd_fn_t(int block, int occ) {
   switch (block) {
-    case 128: return occ ? (const void*)k_backward<128, 4, EXT> : (const void*)k_backward<128, 1, EXT>;
-    case 256: return occ ? (const void*)k_backward<256, 2, EXT> : (const void*)k_backward<256, 1, EXT>;
-    case 512: return (const void*)k_backward<512, 1, EXT>;
+    case 128: return occ ? (const void*)k_backward<128, 4, KIND> : (const void*)k_backward<128, 1, KIND>;
+    case 256: return occ ? (const void*)k_backward<256, 2, KIND> : (const void*)k_backward<256, 1, KIND>;
+    case 512: return (const void*)k_backward<512, 1, KIND>;
   }
   return nullptr;
 }
-static const void* bwd_fn(int block, int occ, bool ext) {
-  return ext ? bwd_fn_t<true>(block, occ) : bwd_fn_t<false>(block, occ);
+static const void* bwd_fn(int block, int occ, int kind) {
+  switch (kind) {
+    case KB_BASIC: return bwd_fn_t<KB_BASIC>(block, occ);
+    case KB_EXT: return bwd_fn_t<KB_EXT>(block, occ);
+    case KB_L2: return bwd_fn_t<KB_L2>(block, occ);
+  }
+  return nullptr;
 }
 static const void* dir_fn(int block) {
   switch (block) {
@@ -202,21 +220,21 @@ static const void* dir_fn(int block) {
   return nullptr;
 }
 
-cudaError_t set_backward_smem_limit(int block, int occ, bool ext, size_t smem) {
-  const void* f = bwd_fn(block, occ, ext);
+cudaError_t set_backward_smem_limit(int block, int occ, int kind, size_t smem) {
+  const void* f = bwd_fn(block, occ, kind);
   if (!f) return cudaErrorInvalidValue;
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t backward_occupancy(int block, int occ, bool ext, size_t smem, int* ctas) {
-  const void* f = bwd_fn(block, occ, ext);
+cudaError_t backward_occupancy(int block, int occ, int kind, size_t smem, int* ctas) {
+  const void* f = bwd_fn(block, occ, kind);
   if (!f) return cudaErrorInvalidValue;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, block, smem);
 }
 
-cudaError_t launch_backward(const KArgs& a, int block, int occ, bool ext, int grid, size_t smem,
+cudaError_t launch_backward(const KArgs& a, int block, int occ, int kind, int grid, size_t smem,
                             cudaStream_t st) {
-  const void* f = bwd_fn(block, occ, ext);
+  const void* f = bwd_fn(block, occ, kind);
   if (!f) return cudaErrorInvalidValue;
   void* args[] = {const_cast<KArgs*>(&a)};
   return cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, st);

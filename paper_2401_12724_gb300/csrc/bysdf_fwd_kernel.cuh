@@ -11,8 +11,6 @@ template <int OP, int BLOCK, int ITEMS, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bars[2 * (BLOCK / 32)];
-  constexpr bool kWo = (OP & (OPF_EVAL | OPF_PDF)) != 0;
-  constexpr bool kU = (OP & OPF_SAMPLE) != 0;
   // each warp's order list (32 * ITEMS entries) and bucket counts (32)
   // behind the tables
   uint32_t* list = reinterpret_cast<uint32_t*>(smem + a.order_off) +
@@ -36,7 +34,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
       if (e == 0xffffffffu) continue;
       const int64_t i = begin + (e & 0xffu);
       Record q;
-      load_record(a, i, kWo, kU, q);
+      load_record(a, i, (OP & (OPF_EVAL | OPF_PDF)) != 0, (OP & OPF_SAMPLE) != 0, q);
       const MatDev* m;
       if (mat >= 0) {
         q.mat = mat;
@@ -44,7 +42,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
       } else {
         q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
-        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
+        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.sstride);
       }
       // two plies side by side in the trace when registers allow (<= 128)
       forward_record<OP, (BLOCK * MINB <= 512 ? 2 : 1)>(

@@ -14,17 +14,36 @@ enum : uint32_t { ERR_TABLE_WAIT = 1u, ERR_TABLE_INFLIGHT = 2u };
 
 // Workspace layout (bytes): [0, 256) control words, then tile_start[n_mat + 1]
 // (int32), then per-tile gradient partials (deterministic backward).
+//
+// Control words.  Every launch gets an epoch e from the host (40 bits,
+// never 0).  err_word = e << 24 | error bits, e the epoch of the launch that
+// last claimed it.  At its start each CTA claims the error word for its
+// launch: a word holding another epoch (a previous launch's, the contents
+// of a fresh allocation, or 0 after bysdf_workspace_error read it) is set
+// to e << 24.  The bits stay until bysdf_workspace_error reads them; a
+// captured launch replayed with its one epoch adds to the bits of its
+// earlier replays until then.
+//
+// tile_word counts the warp-tile draws.  For records in any order with
+// fewer than 2^24 draws (claim_tiles) the CTAs claim it the same way and
+// the draws count from e << 24; the launch's last draw sets it to 0, so the
+// next launch (a replay with the same epoch too) claims it again, and no
+// reset kernel runs.  Otherwise the host launches k_plan first, which sets
+// tile_word to 0 and err_word to e << 24 (and, for material-sorted records,
+// computes the first tile of every material).
 constexpr size_t kWsCtl = 256;
+constexpr int kEpochShift = 24;
 struct WsCtl {
-  int32_t tile_counter;
-  uint32_t err;
-  int32_t pad[62];
+  unsigned long long tile_word;
+  unsigned long long err_word;
+  int32_t pad[60];
 };
 
 struct KArgs {
   const uint8_t* table;  // device material table (n_mat blocks of `stride` bytes)
   int32_t n_mat;
-  int32_t stride;
+  int32_t stride;        // bytes of one material's table (global memory)
+  int32_t sstride;       // MODE_ALL_SMEM: bytes between materials' tables in shared memory
   int32_t mode;
   int32_t tile;          // records per warp tile (32 * items)
   int64_t n;
@@ -39,6 +58,9 @@ struct KArgs {
   const float* grad_f;
   float* grad_params;
   float* partials;       // deterministic backward: [n_tiles][n_param]
+  const float* target;   // L2 backward: target radiance (3 planes); NULL otherwise
+  const float* weight;   // L2 backward: per-record loss weights, or NULL (1)
+  float* loss_mat;       // L2 backward: per-material loss, or NULL
   int32_t n_param;       // gradient columns: 8, or 15 (extended set)
   int32_t order_off;      // forward: byte offset of the warps' sort keys in shared memory
   float *grad_wi, *grad_wo;  // direction backward: 3 planes each, or NULL
@@ -47,7 +69,8 @@ struct KArgs {
   uint32_t stoch_flags;      //   STOCH_* bits
   uint32_t wait_limit;       // polls of a table-copy wait before it gives up
   uint32_t test_stall;       // test hook: table waits poll a barrier nothing arrives on
-  uint32_t pad_st;
+  uint32_t claim_tiles;      // the tile count starts at epoch << 24 (no k_plan launched)
+  uint64_t epoch;            // this launch's epoch (control words)
   WsCtl* ctl;
   const int32_t* tile_start;
 };
@@ -91,6 +114,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Sets `word` to epoch << 24 unless it already carries this epoch.  Writers
+// of another epoch cannot run at the same time (the calls that share a
+// workspace are stream-ordered), so at most one compare-and-swap of the
+// CTAs of a launch succeeds and the loop ends after a few turns; it is
+// bounded all the same.
+__device__ __forceinline__ void claim_word(unsigned long long* word, uint64_t epoch) {
+  const unsigned long long mine = (unsigned long long)epoch << kEpochShift;
+  unsigned long long cur = atomicAdd(word, 0ull);
+  for (int it = 0; it < 64 && (cur >> kEpochShift) != epoch; ++it) {
+    const unsigned long long prev = atomicCAS(word, cur, mine);
+    if (prev == cur) break;
+    cur = prev;
+  }
+}
+
+// Error bits of this launch (after the CTA claimed the word).
+__device__ __forceinline__ void set_error(WsCtl* ctl, uint32_t code) {
+  atomicOr(&ctl->err_word, (unsigned long long)code);
+}
+
 // Bounded wait: gives up after `limit` polls (each poll may itself suspend
 // for a hardware-defined interval), records the failure and returns false.
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -98,7 +141,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
                                                   uint32_t code, uint32_t limit = kWaitLimit) {
   for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
-  atomicOr(&ctl->err, code);
+  set_error(ctl, code);
   return false;
 }
 
@@ -220,17 +263,37 @@ __device__ __forceinline__ void forward_record(const KArgs& a, const MatDev& m,
   }
 }
 
+// Kinds of the backward: the 8 parameters of the basic set, the 15 of the
+// extended set, and the basic set with the upstream gradient taken from an
+// L2 loss against target radiance, whose value is a ninth column.
+enum { KB_BASIC = 0, KB_EXT = 1, KB_L2 = 2 };
+template <int KIND> struct KbCols {
+  static constexpr int grad = KIND == KB_EXT ? 15 : 8;            // gradient columns
+  static constexpr int acc = KIND == KB_L2 ? 9 : grad;             // accumulated columns
+};
+
 // Gradient of sum_c g_c f_c of one record w.r.t. the material parameters:
-// the 8 of the basic set (EXT false; [0..2] moves both body colours) or the
-// 15 of the extended set (EXT true; layout of bysdf_set_params_ext).
-template <bool EXT>
+// the 8 of the basic set ([0..2] moves both body colours), or the 15 of the
+// extended set (KB_EXT; layout of bysdf_set_params_ext).  KB_L2: g_c =
+// 2 w (f_c - target_c) from the record's own f (Sec. 5.2 fitting of an L2
+// loss), gout[8] = w sum_c (f_c - target_c)^2, and f is written to
+// a.f_rgb when given (0 where the record has no valid evaluation).
+template <int KIND>
 __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
                                                 const float2* map, int64_t i, Record& q,
                                                 float* gout) {
   typedef DualF<ND> D;
-  constexpr int NP = EXT ? 15 : 8;
+  constexpr bool EXT = KIND == KB_EXT;
+  constexpr int NA = KbCols<KIND>::acc;
 #pragma unroll
-  for (int k = 0; k < NP; ++k) gout[k] = 0.f;
+  for (int k = 0; k < NA; ++k) gout[k] = 0.f;
+  if constexpr (KIND == KB_L2) {
+    if (a.f_rgb) {
+      a.f_rgb[i] = 0.f;
+      a.f_rgb[a.n + i] = 0.f;
+      a.f_rgb[2 * a.n + i] = 0.f;
+    }
+  }
   if (!record_valid(q, a.n_mat, true, a.ratio != nullptr, false)) return;
   const MatVars<D> mv = mat_vars<D>(m);
   Geo<D> G;
@@ -242,10 +305,29 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   float dln_a[2] = {0.f, 0.f};
   eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L, dln_a);
   const int64_t n = a.n;
-  const float g0 = __ldcg(a.grad_f + i), g1 = __ldcg(a.grad_f + n + i),
-              g2 = __ldcg(a.grad_f + 2 * n + i);
   // f_c = spec + k^B_c body, with k^B = k^B_x (reflection side) or k^B_y
   const float* kb = L.refl ? m.alb : m.alb_y;
+  float g0, g1, g2;
+  if constexpr (KIND == KB_L2) {
+    const float f0 = L.spec.v + kb[0] * L.body.v, f1 = L.spec.v + kb[1] * L.body.v,
+                f2 = L.spec.v + kb[2] * L.body.v;
+    if (a.f_rgb) {
+      a.f_rgb[i] = f0;
+      a.f_rgb[n + i] = f1;
+      a.f_rgb[2 * n + i] = f2;
+    }
+    const float w = a.weight ? __ldcg(a.weight + i) : 1.0f;
+    const float d0 = f0 - __ldcg(a.target + i), d1 = f1 - __ldcg(a.target + n + i),
+                d2 = f2 - __ldcg(a.target + 2 * n + i);
+    g0 = 2.0f * w * d0;
+    g1 = 2.0f * w * d1;
+    g2 = 2.0f * w * d2;
+    gout[8] = w * (d0 * d0 + d1 * d1 + d2 * d2);
+  } else {
+    g0 = __ldcg(a.grad_f + i);
+    g1 = __ldcg(a.grad_f + n + i);
+    g2 = __ldcg(a.grad_f + 2 * n + i);
+  }
   const float gs = g0 + g1 + g2;
   const float gb = g0 * kb[0] + g1 * kb[1] + g2 * kb[2];
   const float body = L.body.v;
@@ -319,14 +401,25 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
   const uint32_t limit = a.wait_limit ? a.wait_limit : kWaitLimit;
   __shared__ int s_ok;
   bool aborted = false;
+  if (threadIdx.x == 0) {
+    claim_word(&a.ctl->err_word, a.epoch);
+    if (a.claim_tiles) claim_word(&a.ctl->tile_word, a.epoch);
+    __threadfence();
+  }
+  __syncthreads();
   if (a.mode == MODE_ALL_SMEM) {
     if (threadIdx.x == 0) {
       mbar_init(&bars[0], 1);
       mbar_init(&stall[0], 1);
       fence_mbar_init();
-      const uint32_t bytes = (uint32_t)a.n_mat * (uint32_t)a.stride;
-      mbar_arrive_tx(&bars[0], bytes);
-      bulk_g2s(smem, a.table, bytes, &bars[0]);
+      // one bulk copy per table, each placed sstride bytes after the last:
+      // the padding shifts every table's header to other banks, so lanes of
+      // one round that read the same field of different materials' tables
+      // do not collide in one bank
+      mbar_arrive_tx(&bars[0], (uint32_t)a.n_mat * (uint32_t)a.stride);
+      for (int k = 0; k < a.n_mat; ++k)
+        bulk_g2s(smem + (size_t)k * a.sstride, a.table + (size_t)k * a.stride,
+                 (uint32_t)a.stride, &bars[0]);
       int ok = mbar_wait_bounded(a.test_stall ? &stall[0] : &bars[0], 0, a.ctl, ERR_TABLE_WAIT,
                                  limit);
       if (!ok) mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_INFLIGHT);
@@ -347,9 +440,21 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
   uint8_t* slot = smem + (size_t)warp * a.stride;
   uint32_t parity = 0;
   int cur = -1;
+  // Every warp draws until it gets a tile past the end, so a launch makes
+  // exactly n_tiles + (its warps) draws.  With claim_tiles the warp that
+  // makes the last one sets the word to 0, the state in which every launch
+  // (a replay of a captured launch with the same epoch too) reclaims it.
+  const unsigned long long tile_base =
+      a.claim_tiles ? (unsigned long long)a.epoch << kEpochShift : 0ull;
+  const unsigned long long last_draw =
+      a.claim_tiles ? (unsigned long long)n_tiles + gridDim.x * (BLOCK / 32) - 1 : ~0ull;
   for (;;) {
     int tile = 0;
-    if (lane == 0) tile = atomicAdd(&a.ctl->tile_counter, 1);
+    if (lane == 0) {
+      const unsigned long long t = atomicAdd(&a.ctl->tile_word, 1ull) - tile_base;
+      if (t == last_draw) atomicExch(&a.ctl->tile_word, 0ull);
+      tile = (int)t;
+    }
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= n_tiles) break;
     int64_t begin, end;
@@ -441,7 +546,7 @@ __device__ __forceinline__ void tile_order(const KArgs& a, const uint8_t* smem, 
       } else {
         mm = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         mm = (mm >= 0 && mm < a.n_mat) ? mm : 0;
-        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.stride);
+        m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.sstride);
       }
       const int K = footprint(__ldcg(a.h + i), __ldcg(a.ratio + i), m->kmax).K;
       b[j] = record_bucket(K, m->np);

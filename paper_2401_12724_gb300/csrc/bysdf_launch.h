@@ -25,14 +25,15 @@ cudaError_t launch_forward(int op, const KArgs& a, int block, int occ, int grid,
                            cudaStream_t st);
 cudaError_t launch_plain(int op, const KArgs& a, int mat, int64_t begin, int64_t end,
                          cudaStream_t st);
-// ext: the 15-column extended parameter set (a.n_param must match)
-cudaError_t launch_backward(const KArgs& a, int block, int occ, bool ext, int grid, size_t smem,
+// kind: KB_BASIC (8 columns), KB_EXT (15), KB_L2 (8 + the loss column); a.n_param
+// must be the accumulated column count (8, 15, 9)
+cudaError_t launch_backward(const KArgs& a, int block, int occ, int kind, int grid, size_t smem,
                             cudaStream_t st);
 cudaError_t launch_reduce_partials(const KArgs& a, cudaStream_t st);
 cudaError_t set_forward_smem_limit(int op, int block, int items, int occ, size_t smem);
-cudaError_t set_backward_smem_limit(int block, int occ, bool ext, size_t smem);
+cudaError_t set_backward_smem_limit(int block, int occ, int kind, size_t smem);
 cudaError_t forward_occupancy(int op, int block, int items, int occ, size_t smem, int* ctas);
-cudaError_t backward_occupancy(int block, int occ, bool ext, size_t smem, int* ctas);
+cudaError_t backward_occupancy(int block, int occ, int kind, size_t smem, int* ctas);
 // direction vector-Jacobian products (a.grad_wi / a.grad_wo)
 cudaError_t set_dirgrad_smem_limit(int block, size_t smem);
 cudaError_t dirgrad_occupancy(int block, size_t smem, int* ctas);

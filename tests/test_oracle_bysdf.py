@@ -407,3 +407,25 @@ def test_extended_gradient_agrees_with_eight_parameter_set(orc):
                                atol=1e-12)
     np.testing.assert_allclose(grad8[:, 3:8], grad15[:, 3:8], rtol=1e-12, atol=1e-12)
 
+
+
+def test_l2_loss_is_multimodal_in_the_helix_angles(orc):
+    """Why the fitting tests leave the helix angles alone: within 4% of the
+    true angles, over a stretch of yarn only two radii long, the L2 loss
+    against the true radiance already has several local minima in each
+    angle -- the ply and fiber phases, and the fiber pattern under the hit
+    point, cycle as the angles move -- so gradient steps from a start a few
+    percent off need not reach the true values (their gradients are still
+    checked against finite differences and against the GPU)."""
+    mats0 = I.materials(5)[:4]
+    rec = I.random_records(4096, n_mat=4, seed=65, wi_mode="cosine", sorted_ids=True, v_max=2.0)
+    tgt, _, st = orc.eval_records(mats0, rec, threads=8)
+    for key in ("ply_twist_deg", "fiber_twist_deg"):
+        loss = []
+        for e in np.linspace(-0.04, 0.04, 81):
+            mats = [dict(m, **{key: m[key] * (1 + e)}) for m in mats0]
+            f, _, _ = orc.eval_records(mats, rec, threads=8)
+            loss.append((((f - tgt) ** 2) * (st == 0)).sum())
+        d = np.diff(np.array(loss))
+        minima = int(((d[:-1] < 0) & (d[1:] > 0)).sum())
+        assert minima >= 3, (key, minima)

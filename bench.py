@@ -629,12 +629,18 @@ def other_workloads(api, N, torch, args, sm_count):
             api.eval(M, d, out=o)
     ms_g, _ = timed(g1.replay, steps, 3)
     ms_g /= calls
+    # the plain form: one launch, one thread per record
+    seg1 = np.array([0, n], np.int64)
+    po = dict(f=o["f"], wo=torch.empty(3, n, device="cuda"),
+              weight=torch.empty(3, n, device="cuda"), pdf=o["pdf"], status=o["status"])
+    ms_p, _ = timed(lambda: api.plain(N.OP_EVAL, M, d, seg1, out=po), steps * 4, 3)
     res[I.WORKLOAD_NAME[1]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
                                    roofline_frac=frac(OPS[1]["eval"], n, ms, sm_count),
                                    graph_ms_per_call=ms_g,
                                    graph_records_per_s=n / (ms_g / 1e3),
-                                   graph_roofline_frac=frac(OPS[1]["eval"], n, ms_g, sm_count))
-    del g1
+                                   graph_roofline_frac=frac(OPS[1]["eval"], n, ms_g, sm_count),
+                                   plain_records_per_s=n / (ms_p / 1e3))
+    del g1, po
     # multi-scale: fused eval + sample
     mats = I.materials(3)
     M = api.Materials(mats)
@@ -645,10 +651,15 @@ def other_workloads(api, N, torch, args, sm_count):
     # the stochastic estimators (jittered nodes + GGX-sampled entry)
     ms_st, _ = timed(lambda: api.eval_sample_pdf_stochastic(M, d, 1, 3, out=o),
                      max(3, steps // 4), 2)
+    # the plain form of the fused op on the same records sorted by material
+    # (sorted outside the timed region)
+    ds, seg3 = sorted_copy(d, len(mats))
+    ms_p, _ = timed(lambda: api.plain_fused(M, ds, seg3, out=o), max(3, steps // 2), 2)
     res[I.WORKLOAD_NAME[3]] = dict(records_per_s=n / (ms / 1e3), ms=ms, records=n,
                                    roofline_frac=frac(OPS[3]["fused"], n, ms, sm_count),
-                                   stochastic_records_per_s=n / (ms_st / 1e3))
-    del d, o
+                                   stochastic_records_per_s=n / (ms_st / 1e3),
+                                   plain_fused_records_per_s=n / (ms_p / 1e3))
+    del d, o, ds
     torch.cuda.empty_cache()
     # fiber migration (Sec. 3.5): the workload-2 records and materials, each
     # material with 2 map pairs switched along the yarn (tables still fit in

@@ -114,17 +114,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Sets `word` to epoch << 24 unless it already carries this epoch.  Writers
+// Sets `word` to epoch << 24 unless it already carries this epoch.  The
+// first compare-and-swap guesses 0 (a claimed tile word returns to 0 at the
+// end of its launch), the next ones the value the last one found.  Writers
 // of another epoch cannot run at the same time (the calls that share a
 // workspace are stream-ordered), so at most one compare-and-swap of the
 // CTAs of a launch succeeds and the loop ends after a few turns; it is
 // bounded all the same.
 __device__ __forceinline__ void claim_word(unsigned long long* word, uint64_t epoch) {
   const unsigned long long mine = (unsigned long long)epoch << kEpochShift;
-  unsigned long long cur = atomicAdd(word, 0ull);
-  for (int it = 0; it < 64 && (cur >> kEpochShift) != epoch; ++it) {
+  unsigned long long cur = 0ull;
+  for (int it = 0; it < 64; ++it) {
     const unsigned long long prev = atomicCAS(word, cur, mine);
-    if (prev == cur) break;
+    if (prev == cur || (prev >> kEpochShift) == epoch) break;
     cur = prev;
   }
 }
@@ -396,18 +398,21 @@ __device__ __forceinline__ void abort_tile(const KArgs& a, int64_t begin, int64_
 template <int BLOCK, class Body>
 __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, uint64_t* bars,
                                                 Body&& body) {
+  static_assert(BLOCK >= 64 && BLOCK % 32 == 0, "thread 32 claims the tile word");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* stall = bars + BLOCK / 32;
   const uint32_t limit = a.wait_limit ? a.wait_limit : kWaitLimit;
   __shared__ int s_ok;
   bool aborted = false;
-  if (threadIdx.x == 0) {
-    claim_word(&a.ctl->err_word, a.epoch);
-    if (a.claim_tiles) claim_word(&a.ctl->tile_word, a.epoch);
-    __threadfence();
-  }
-  __syncthreads();
+  // with claim_tiles the CTA claims the control words for its launch (else
+  // k_plan set them): thread 0 the error word, before it can set an error
+  // bit, and thread 32 the tile word, both while the table copies are in
+  // flight; no warp draws a tile before the barrier after them
   if (a.mode == MODE_ALL_SMEM) {
+    if (threadIdx.x == 32 && a.claim_tiles) {
+      claim_word(&a.ctl->tile_word, a.epoch);
+      __threadfence();
+    }
     if (threadIdx.x == 0) {
       mbar_init(&bars[0], 1);
       mbar_init(&stall[0], 1);
@@ -420,6 +425,7 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
       for (int k = 0; k < a.n_mat; ++k)
         bulk_g2s(smem + (size_t)k * a.sstride, a.table + (size_t)k * a.stride,
                  (uint32_t)a.stride, &bars[0]);
+      if (a.claim_tiles) claim_word(&a.ctl->err_word, a.epoch);
       int ok = mbar_wait_bounded(a.test_stall ? &stall[0] : &bars[0], 0, a.ctl, ERR_TABLE_WAIT,
                                  limit);
       if (!ok) mbar_wait_bounded(&bars[0], 0, a.ctl, ERR_TABLE_INFLIGHT);
@@ -428,6 +434,14 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
     __syncthreads();
     aborted = !s_ok;
   } else {
+    if (a.claim_tiles) {
+      if (threadIdx.x == 0) {
+        claim_word(&a.ctl->err_word, a.epoch);
+        claim_word(&a.ctl->tile_word, a.epoch);
+        __threadfence();
+      }
+      __syncthreads();
+    }
     if (lane == 0) {
       mbar_init(&bars[warp], 1);
       mbar_init(&stall[warp], 1);

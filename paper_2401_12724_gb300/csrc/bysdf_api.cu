@@ -345,14 +345,15 @@ size_t ws_partials_off(int n_mat) { return align_up(kWsCtl + 4 * (size_t)(n_mat 
 int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
 
 // Defaults measured on GB300 with the benchmark workloads (eval + sample +
-// pdf over 2^24 records; forward + backward over 2^22): 16 warps per SM in
-// CTAs of 512; four records per lane per warp tile for the forward calls
-// (tiles of 128 sort into rounds of equal ply counts; 1.6% over two), two
-// for the backward.  bysdf_autotune refines them for a given record set.
+// pdf over 2^24 records; forward + backward over 2^24 material-sorted
+// records of 64 materials): 16 warps per SM in CTAs of 512; four records
+// per lane per warp tile for the forward calls (two or eight within 0.3%),
+// eight for the backward (per 2^24 records 2.35 ms, against 2.42 ms at four
+// and 3.10 ms at two).  bysdf_autotune refines them for a given record set.
 bysdf_launch_config default_cfg(int op) {
   bysdf_launch_config c;
   c.block = 512;
-  c.items = op == BYSDF_OP_BACKWARD ? 2 : 4;
+  c.items = op == BYSDF_OP_BACKWARD ? 8 : 4;
   c.ctas_per_sm = 0;  // 0: as many as fit
   c.occupancy = 0;
   return c;
@@ -606,9 +607,10 @@ struct L2Args {
 };
 int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const float* grad_f,
                  float* grad_params, int deterministic, void* ws, size_t ws_bytes,
-                 cudaStream_t st, const bysdf_launch_config& c, int kind = KB_BASIC,
+                 cudaStream_t st, const bysdf_launch_config& cfg, int kind = KB_BASIC,
                  float* grad_wi = nullptr, float* grad_wo = nullptr,
                  const L2Args* l2 = nullptr) {
+  bysdf_launch_config c = cfg;
   const bool ext = kind == KB_EXT;
   const int ng = ext ? BYSDF_NPARAM_EXT : BYSDF_NPARAM;   // gradient columns
   const int np = kind == KB_L2 ? ng + 1 : ng;             // accumulated columns
@@ -657,7 +659,14 @@ int run_backward(const bysdf_materials* m, const bysdf_hits* h, int64_t n, const
   BY_CU(backward_occupancy(c.block, c.occupancy, kind, smem, &occ));
   if (!deterministic) BY_CU(cudaMemsetAsync(grad_params, 0, sizeof(float) * ng * m->n_mat, st));
   const int grid = grid_for(m, c, occ);
-  if ((rc = plan(m, a, ws, st, (int64_t)grid * (c.block / 32)))) return rc;
+  // fewer warp tiles than resident warps leaves warps idle: the tile is
+  // halved until the batch covers them (n / tile tiles for records in any
+  // order; material-sorted records have at least as many)
+  const int64_t warps = (int64_t)grid * (c.block / 32);
+  while (c.items > 1 && (n + 32 * c.items - 1) / (32 * c.items) < warps) c.items /= 2;
+  a.tile = 32 * c.items;
+  a.n_tiles = (n + a.tile - 1) / a.tile;
+  if ((rc = plan(m, a, ws, st, warps))) return rc;
   BY_CU(launch_backward(a, c.block, c.occupancy, kind, grid, smem, st));
   if (deterministic) BY_CU(launch_reduce_partials(a, st));
   if (grad_wi || grad_wo) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace bysdf {
@@ -323,14 +324,32 @@ template <class S> __device__ __forceinline__ V3<S> operator-(const V3<S>& a) {
 template <class S, class T> __device__ __forceinline__ V3<S> operator*(const V3<S>& a, const T& s) {
   return mk3<S>(a.x * s, a.y * s, a.z * s);
 }
-template <class S> __device__ __forceinline__ S dot(const V3<S>& a, const V3<S>& b) {
+// a float vector may meet a dual one (a direction without tangents against
+// the frame): the products then carry only the dual side's tangents
+template <class A, class B> __device__ __forceinline__ auto dot(const V3<A>& a, const V3<B>& b) {
   return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <int N>
+__device__ __forceinline__ V3<DualF<N>> operator+(const V3<DualF<N>>& a, const V3<float>& b) {
+  return mk3<DualF<N>>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+template <int N>
+__device__ __forceinline__ V3<DualF<N>> operator+(const V3<float>& a, const V3<DualF<N>>& b) {
+  return mk3<DualF<N>>(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+// a float vector as S (no tangents), or the vector itself
+template <class S, class W> __device__ __forceinline__ V3<S> as3(const V3<W>& w) {
+  if constexpr (std::is_same<S, W>::value) {
+    return w;
+  } else {
+    return mk3<S>(S(w.x), S(w.y), S(w.z));
+  }
 }
 template <class S> __device__ __forceinline__ V3<S> cross(const V3<S>& a, const V3<S>& b) {
   return mk3<S>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 template <class S> __device__ __forceinline__ V3<S> normalize(const V3<S>& a) {
-  return a * (S(1.0f) / xsqrt(dot(a, a)));
+  return a * (1.0f / xsqrt(dot(a, a)));
 }
 
 }  // namespace bysdf

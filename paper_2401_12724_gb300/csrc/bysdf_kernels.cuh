@@ -305,7 +305,7 @@ __device__ __forceinline__ void backward_record(const KArgs& a, const MatDev& m,
   make_shade(m, mv, G, q, s);
   LobeVals<D> L;
   float dln_a[2] = {0.f, 0.f};
-  eval_lobes(m, s, lift3<D>(q.wo[0], q.wo[1], q.wo[2]), L, dln_a);
+  eval_lobes(m, s, mk3<float>(q.wo[0], q.wo[1], q.wo[2]), L, dln_a);
   const int64_t n = a.n;
   // f_c = spec + k^B_c body, with k^B = k^B_x (reflection side) or k^B_y
   const float* kb = L.refl ? m.alb : m.alb_y;

@@ -42,8 +42,8 @@ template <class S>
 struct MatVars {
   S kp, kf;             // ply turns / length, fiber map periods / length
   S cos_af, sin_af;     // fiber helix angle
-  S sigma_s;            // shadow density
-  S beta_t, beta_b;     // GGX roughness (radians)
+  float sigma_s;        // shadow density (closed-form derivative)
+  float beta_t, beta_b; // GGX roughness, radians (closed-form derivatives)
   bool seeded;          // helix-angle tangents carried (parameter backward)
 };
 
@@ -56,9 +56,9 @@ __device__ __forceinline__ MatVars<S> mat_vars(const MatDev& m, bool seed_params
   q.kf = S(m.kf_hi + m.kf_lo);
   q.cos_af = S(m.cos_af);
   q.sin_af = S(m.sin_af);
-  q.sigma_s = S(m.sigma_s);
-  q.beta_t = S(m.beta_t);
-  q.beta_b = S(m.beta_b);
+  q.sigma_s = m.sigma_s;
+  q.beta_t = m.beta_t;
+  q.beta_b = m.beta_b;
   q.seeded = false;
   if constexpr (is_dual<S>::value) {
     if (!seed_params) return q;
@@ -213,6 +213,43 @@ __device__ __forceinline__ void migration_maps(const MatDev& m, const float2* ma
   if (vf(*wgt) > 0.f) pick(nb, mp1, wv1);
 }
 
+// Scalar of the ply trace (see node_geometry): the parameter backward's
+// two-tangent dual numbers (alpha_p, alpha_f) with float directions trace
+// with alpha_p alone; every other scalar traces as itself.
+template <class S, class K>
+struct TraceScalar {
+  using type = S;
+};
+template <>
+struct TraceScalar<DualF<ND>, float> {
+  using type = DualF<1>;
+};
+template <class P, class S>
+__device__ __forceinline__ P narrow(const S& x) {
+  if constexpr (std::is_same<P, S>::value) {
+    return x;
+  } else {
+    P r;
+    r.v = x.v;
+    r.d[0] = x.d[D_ALPHA_P];
+    return r;
+  }
+}
+template <class S, class P>
+__device__ __forceinline__ S widen(const P& x) {
+  if constexpr (std::is_same<P, S>::value) {
+    return x;
+  } else {
+    S r(x.v);
+    r.d[D_ALPHA_P] = x.d[0];
+    return r;
+  }
+}
+template <class S, class P>
+__device__ __forceinline__ V3<S> widen3(const V3<P>& x) {
+  return mk3<S>(widen<S>(x.x), widen<S>(x.y), widen<S>(x.z));
+}
+
 template <class S, int PLIES = 2, class K = float>
 __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map,
                                               const MatVars<S>& mv, float X0x, float X0y,
@@ -354,24 +391,30 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   out.hit = true;
   out.ply = best;
   if (trace_only) return;
-  // the closest ply's updates in S with sincospif: ply centre, its phase and
-  // the intersection distance of the last one
-  const S ck = c0v * m.rot_c[best] - s0v * m.rot_s[best];
-  const S sk = s0v * m.rot_c[best] + c0v * m.rot_s[best];
-  S best_t = S(t_start), best_cx = S(0.f), best_cy = S(0.f), best_s = S(0.f), best_c = S(1.f);
+  // the closest ply's updates with sincospif: ply centre, its phase and the
+  // intersection distance of the last one.  In the parameter backward (two
+  // tangents, alpha_p and alpha_f, and float directions) only alpha_p moves
+  // the trace, the ply frame, the ply azimuth and the ply shadowing: that
+  // part runs in P, which carries alpha_p alone (P = S otherwise).
+  using P = typename TraceScalar<S, K>::type;
+  const P kp = narrow<P>(mv.kp);
+  const P c0p = narrow<P>(c0v), s0p = narrow<P>(s0v);
+  const P ck = c0p * m.rot_c[best] - s0p * m.rot_s[best];
+  const P sk = s0p * m.rot_c[best] + c0p * m.rot_s[best];
+  P best_t = P(t_start), best_cx = P(0.f), best_cy = P(0.f), best_s = P(0.f), best_c = P(1.f);
   bool grazed = false;
 #pragma unroll 1
   for (int i = 0; i < n_upd; ++i) {
-    S sd, cd;
-    xsincos_turns(mv.kp * (kappa * best_t), &sd, &cd);
+    P sd, cd;
+    xsincos_turns(kp * (kappa * best_t), &sd, &cd);
     best_c = ck * cd - sk * sd;
     best_s = sk * cd + ck * sd;
     best_cx = Rc * best_c;
     best_cy = Rc * best_s;
-    const S qx = X0x - best_cx, qy = X0y - best_cy;
-    const S b = qx * ex + qy * ey;
-    const S perp = qx * ey - qy * ex;
-    const S disc = (Rp - perp) * (Rp + perp);
+    const P qx = X0x - best_cx, qy = X0y - best_cy;
+    const P b = qx * ex + qy * ey;
+    const P perp = qx * ey - qy * ex;
+    const P disc = (Rp - perp) * (Rp + perp);
     grazed = grazed || !(vf(disc) > 0.f);
     best_t = xmax0(-b - xsqrt(xmax0(disc)));
   }
@@ -386,27 +429,29 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   }
   // Sec. 3.4: hit point, ply normal (from the ply centre, in the circular
   // cross-section), ply tangent (derivative of the helix through x)
-  const S xx = X0x + best_t * ex, xy = X0y + best_t * ey;
-  const S dz = kappa * best_t;
-  out.x = mk3<S>(xx, xy, v + dz);
-  const S dx = xx - best_cx, dy = xy - best_cy;
-  const S inv_dl = S(1.f) / xsqrt(dx * dx + dy * dy);
-  const V3<S> np = mk3<S>(dx * inv_dl, dy * inv_dl, S(0.f));
-  const S wp = (2.0f * kPi) * mv.kp;
-  const V3<S> traw = mk3<S>(-(wp * xy), wp * xx, S(1.f));
-  const V3<S> tp = normalize(traw - np * dot(traw, np));
-  const V3<S> ep = cross(tp, np);
+  const P xx = X0x + best_t * ex, xy = X0y + best_t * ey;
+  const P dz = kappa * best_t;
+  out.x = mk3<S>(widen<S>(xx), widen<S>(xy), widen<S>(v + dz));
+  const P dx = xx - best_cx, dy = xy - best_cy;
+  const P inv_dl = 1.0f / xsqrt(dx * dx + dy * dy);
+  const V3<P> np = mk3<P>(dx * inv_dl, dy * inv_dl, P(0.f));
+  const P wp = (2.0f * kPi) * kp;
+  const V3<P> traw = mk3<P>(-(wp * xy), wp * xx, P(1.f));
+  const V3<P> tp = normalize(traw - np * dot(traw, np));
+  const V3<P> ep = cross(tp, np);
   // Sec. 3.5.1: ply azimuth of the hit about the ply centre, from the ply
   // centre's radial direction; fiber phase in map periods; 1D map lookup
-  const S u_ply = xatan2(best_c * np.y - best_s * np.x, best_c * np.x + best_s * np.y);
-  const S w = u_ply * m.m_over_2pi - phase_f_v - mv.kf * dz;
+  const S u_ply =
+      widen<S>(xatan2(best_c * np.y - best_s * np.x, best_c * np.x + best_s * np.y));
+  const S dzs = widen<S>(dz);
+  const S w = u_ply * m.m_over_2pi - phase_f_v - mv.kf * dzs;
   // map 0, or the migration maps of the hit's segment (Sec. 3.5)
   S delta, of;
   if (m.mig_maps > 1) {
     const float2* mp = map;
     const float2* mp1 = map;
     S wv = w, wv1 = w, wgt = S(0.f);
-    migration_maps(m, map, mv, u_ply, v, dz, w, &mp, &wv, &mp1, &wv1, &wgt);
+    migration_maps(m, map, mv, u_ply, v, dzs, w, &mp, &wv, &mp1, &wv1, &wgt);
     fiber_lookup(mp, m.T, wv, &delta, &of);
     if (vf(wgt) > 0.f) {
       S d1, o1;
@@ -418,29 +463,30 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     fiber_lookup(map, m.T, w, &delta, &of);
   }
   // n_f = n'(R(n_p)), t_f = t'(R(t_p))
-  out.tf = tp * mv.cos_af + ep * mv.sin_af;
+  const V3<S> nps = widen3<S>(np);
+  out.tf = widen3<S>(tp) * mv.cos_af + widen3<S>(ep) * mv.sin_af;
   S sd, cd;
   xsincos(delta, &sd, &cd);
-  out.nf = np * cd + cross(out.tf, np) * sd;
+  out.nf = nps * cd + cross(out.tf, nps) * sd;
   // Sec. 4.1.4: ply shadowing by the in-plane chords through the other
   // plies of this cross-section; fiber shadowing from the map
-  S occ = S(0.f);
+  P occ = P(0.f);
 #pragma unroll 1
   for (int j = 1; j < m.np; ++j) {
     int r = j;
     const float rc = m.rot_c[r], rs = m.rot_s[r];
-    const S cjx = best_cx * rc - best_cy * rs, cjy = best_cx * rs + best_cy * rc;
-    const S qx = xx - cjx, qy = xy - cjy;
-    const S b = qx * wx + qy * wy;
-    const S perp = qx * wy - qy * wx;
-    const S disc = (Rp - perp) * (Rp + perp);
+    const P cjx = best_cx * rc - best_cy * rs, cjy = best_cx * rs + best_cy * rc;
+    const P qx = xx - cjx, qy = xy - cjy;
+    const P b = qx * wx + qy * wy;
+    const P perp = qx * wy - qy * wx;
+    const P disc = (Rp - perp) * (Rp + perp);
     if (vf(disc) > 0.f) {
-      const S sq = xsqrt(disc);
-      const S s2 = sq - b;
+      const P sq = xsqrt(disc);
+      const P s2 = sq - b;
       if (vf(s2) > 0.f) occ = occ + (s2 - xmax0(-b - sq));
     }
   }
-  const S occ_all = occ * m.inv_2Rp + of;
+  const S occ_all = widen<S>(occ) * m.inv_2Rp + of;
   out.g = xexp(-(mv.sigma_s * occ_all));
   out.dg_dsig = -vf(occ_all) * vf(out.g);
 }
@@ -475,7 +521,7 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   const float ex = -cu, ey = -su;
   const K lxy = xsqrt(wi.x * wi.x + wi.y * wi.y);
   if (!(vf(lxy) >= 1e-7f)) return;
-  const K inv_l = K(1.0f) / lxy;
+  const K inv_l = 1.0f / lxy;
   const K kappa = -wi.z * inv_l;
   const K wx = wi.x * inv_l, wy = wi.y * inv_l;
   // ply 0's phase at the hit's cross-section, and the fiber phase there
@@ -549,11 +595,11 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
   const float inv = 1.0f / (float)nhit;
   const S nl = xsqrt(dot(ns, ns));
   if (!(vf(nl) > 1e-9f * (float)nhit)) return;
-  G.n = ns * (S(1.f) / nl);
+  G.n = ns * (1.0f / nl);
   const V3<S> tperp = ts - G.n * dot(ts, G.n);
   const S tl = xsqrt(dot(tperp, tperp));
   if (!(vf(tl) > 1e-9f * (float)nhit)) return;
-  G.t = tperp * (S(1.f) / tl);
+  G.t = tperp * (1.0f / tl);
   G.x = xs * inv;
   G.g = gs * inv;
   G.dg_dsig = dgs * inv;
@@ -584,14 +630,14 @@ __device__ __forceinline__ S fresnel(const S& ci, float eta) {
 }
 // Anisotropic GGX (Heitz 2014) in a local frame (x = t, y = b, z = n).
 template <class S>
-__device__ __forceinline__ S ggx_d(const V3<S>& m, const S& at, const S& ab) {
+__device__ __forceinline__ S ggx_d(const V3<S>& m, float at, float ab) {
   if (!(vf(m.z) > 0.f)) return S(0.f);
   const S mx = m.x / at, my = m.y / ab;
   const S q = mx * mx + my * my + m.z * m.z;
   return S(1.0f / kPi) / (at * ab * q * q);
 }
 template <class S>
-__device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, const S& at, const S& ab) {
+__device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, float at, float ab) {
   if (!(vf(wm) * vf(w.z) > 0.f)) return S(0.f);
   const S an = vf(w.z) < 0.f ? -w.z : w.z;
   const S ax = at * w.x, ay = ab * w.y;
@@ -601,8 +647,8 @@ __device__ __forceinline__ S ggx_g1(const V3<S>& w, const S& wm, const S& at, co
 // direction by its own cosine, which near grazing is a ratio of two small
 // numbers rounded apart; the quotient is formed without them
 template <class S>
-__device__ __forceinline__ S ggx_g1_over_cos(const V3<S>& w, const S& wm, const S& at,
-                                             const S& ab) {
+__device__ __forceinline__ S ggx_g1_over_cos(const V3<S>& w, const S& wm, float at,
+                                             float ab) {
   if (!(vf(wm) * vf(w.z) > 0.f)) return S(0.f);
   const S an = vf(w.z) < 0.f ? -w.z : w.z;
   const S ax = at * w.x, ay = ab * w.y;
@@ -611,13 +657,13 @@ __device__ __forceinline__ S ggx_g1_over_cos(const V3<S>& w, const S& wm, const 
 // GGX visible-normal sample (Heitz 2018), local frame, w.z > 0; the disk
 // point is (r cos phi, r sin phi) with r = sqrt(u0), phi = 2 pi u1.
 template <class S>
-__device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, const S& at, const S& ab,
-                                             float r, float sphi, float cphi) {
+__device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, float at, float ab, float r,
+                                             float sphi, float cphi) {
   const V3<S> V = normalize(mk3<S>(at * w.x, ab * w.y, w.z));
   const S lensq = V.x * V.x + V.y * V.y;
   V3<S> T1 = lift3<S>(1.f, 0.f, 0.f);
   if (vf(lensq) > 0.f) {
-    const S il = S(1.f) / xsqrt(lensq);
+    const S il = 1.0f / xsqrt(lensq);
     T1 = mk3<S>(-(V.y * il), V.x * il, S(0.f));
   }
   const V3<S> T2 = cross(V, T1);
@@ -629,8 +675,8 @@ __device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, const S& at, const 
   return normalize(mk3<S>(at * Nh.x, ab * Nh.y, xmax0(Nh.z)));
 }
 
-template <class S>
-__device__ __forceinline__ V3<S> to_local(const V3<S>& w, const V3<S>& t, const V3<S>& b,
+template <class W, class S>
+__device__ __forceinline__ V3<S> to_local(const V3<W>& w, const V3<S>& t, const V3<S>& b,
                                           const V3<S>& n) {
   return mk3<S>(dot(w, t), dot(w, b), dot(w, n));
 }
@@ -639,7 +685,8 @@ __device__ __forceinline__ V3<S> to_local(const V3<S>& w, const V3<S>& t, const 
 template <class S>
 struct Shade {
   V3<S> t, b, n, wi;
-  S mui, at, ab, g, fr;
+  S mui, g, fr;
+  float at, ab;           // GGX roughness (no tangents: closed-form derivatives)
   bool at_free, ab_free;  // roughness not clamped (its derivative passes)
   S body_x0;  // G / (1 + a(mu_i)): f_x^B per unit r B k^B_x before its angular term
   S body_y0;  // G / pi: f_y^B per unit (1 - r) B k^B_y per unit cosine
@@ -657,22 +704,23 @@ __device__ __forceinline__ S clamp_alpha(const S& a) {
   return a;
 }
 
-// wi: the record's incoming direction as S (seeded for direction tangents);
-// sc: the stochastic estimators' state (GGX-sampled entry), or NULL
-template <class S>
+// wi: the record's incoming direction, float (no tangents) or S (seeded for
+// direction tangents); sc: the stochastic estimators' state (GGX-sampled
+// entry), or NULL
+template <class S, class W>
 __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
-                                           const Geo<S>& G, const V3<S>& wi, Shade<S>& s,
+                                           const Geo<S>& G, const V3<W>& wi, Shade<S>& s,
                                            const StochCtx* sc = nullptr) {
-  s.wi = wi;
+  s.wi = as3<S>(wi);
   s.n = G.n;
   s.t = G.t;
   s.b = cross(s.n, s.t);
   // reading: two-sided shading, the side of omega_i is outside at x
-  if (vf(dot(s.wi, s.n)) < 0.f) {
+  if (vf(dot(wi, s.n)) < 0.f) {
     s.n = -s.n;
     s.b = -s.b;
   }
-  s.mui = dot(s.wi, s.n);
+  s.mui = dot(wi, s.n);
   // Sec. 4.2: beta_multi = beta + (h2 - h1) / 2 (reading), GGX alpha = beta
   const float hw = 0.5f * G.width;
   s.at = clamp_alpha(mv.beta_t + hw);
@@ -685,7 +733,7 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   // 1 + a(mu_i), a(mu) = (1 - mu ln(1 + 1/mu)) / 2; Eq. 6: Lambert
   s.body_x0 = S(0.f);
   if (vf(s.mui) > 0.f) {
-    const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + S(1.f) / s.mui));
+    const S aLS = 0.5f * (1.0f - s.mui * xlog(1.0f + 1.0f / s.mui));
     s.body_x0 = s.g / (1.0f + aLS);
   }
   s.body_y0 = s.g * (1.0f / kPi);
@@ -704,14 +752,14 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
     const float v0 = unit24(rnd.w[0]), v1 = unit24(rnd.w[1]);
     float sphi, cphi;
     sincospif(2.0f * v1, &sphi, &cphi);
-    const V3<S> ml = vndf_sample(to_local(s.wi, s.t, s.b, s.n), s.at, s.ab, sqrtf(v0), sphi, cphi);
+    const V3<S> ml = vndf_sample(to_local(wi, s.t, s.b, s.n), s.at, s.ab, sqrtf(v0), sphi, cphi);
     mn = s.t * ml.x + s.b * ml.y + s.n * ml.z;
-    ci = dot(s.wi, mn);
+    ci = dot(wi, mn);
   }
   const S s2t = (1.0f - ci * ci) * (m.inv_eta * m.inv_eta);
   if (!(vf(s.mui) > 0.f) || !(vf(ci) > 0.f) || !(vf(s2t) < 1.0f)) return;
   const S ct = xsqrt(1.0f - s2t);
-  const V3<S> din = s.wi * (-m.inv_eta) + mn * (ci * m.inv_eta - ct);
+  const V3<S> din = wi * (-m.inv_eta) + mn * (ci * m.inv_eta - ct);
   if (rough && !(vf(dot(din, s.n)) < 0.f)) return;
   const S a = din.x * din.x + din.y * din.y;
   if (!(vf(a) > 1e-12f)) return;
@@ -720,7 +768,7 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   const S disc = xmax0(bq * bq - a * c);
   const S sy = xmax0((xsqrt(disc) - bq) / a);
   const S yx = G.x.x + din.x * sy, yy = G.x.y + din.y * sy;
-  const S il = S(1.f) / xsqrt(yx * yx + yy * yy);
+  const S il = 1.0f / xsqrt(yx * yx + yy * yy);
   s.ny = mk3<S>(yx * il, yy * il, S(0.f));
   s.by = mk3<S>(s.ny.y, -s.ny.x, S(0.f));  // n_y x z
   s.iy = -din;
@@ -732,7 +780,7 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
 template <class S>
 __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv,
                                            const Geo<S>& G, const Record& q, Shade<S>& s) {
-  make_shade(m, mv, G, lift3<S>(q.wi[0], q.wi[1], q.wi[2]), s);
+  make_shade(m, mv, G, mk3<float>(q.wi[0], q.wi[1], q.wi[2]), s);
 }
 
 // f |wo.n| of the four lobes at wo; spec = f_x^S + f_y^S (grey), body = the
@@ -767,8 +815,9 @@ __device__ __forceinline__ void dln_ggx_g1(float wx, float wy, float wz, float a
   *db = -ab * wy * wy * k;
 }
 
-template <class S>
-__device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, const V3<S>& wo,
+// wo: float (no tangents) or S (seeded for direction tangents)
+template <class S, class W>
+__device__ __forceinline__ void eval_lobes(const MatDev& m, const Shade<S>& s, const V3<W>& wo,
                                            LobeVals<S>& L, float* dln_alpha = nullptr) {
   L.spec = S(0.f);
   L.body = S(0.f);

@@ -488,6 +488,16 @@ int bysdf_noalloc_error(void* stream, uint32_t* err);
  * fault, no hang: every wait stays bounded. */
 int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls);
 
+/* Test hook of the host-side allocation-failure path (no counterpart in the
+ * paper): the next `count` device allocations of the library (the material
+ * table of bysdf_create_materials, the device slots of
+ * bysdf_host_pipeline_create) fail as on an exhausted device, without calling
+ * cudaMalloc: the call returns BYSDF_E_CUDA ("cudaMalloc: out of memory"),
+ * writes no handle and frees what it had taken.  count = 0 switches the hook
+ * off; every other entry point allocates nothing and is unaffected.
+ * Process-wide.  Returns BYSDF_E_ARG for count < 0. */
+int bysdf_test_fail_allocations(int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

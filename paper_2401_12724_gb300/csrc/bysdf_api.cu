@@ -56,6 +56,18 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
+// Every device allocation of the library goes through dev_alloc.  Test hook
+// (bysdf_test_fail_allocations): while g_fail_allocs > 0, an allocation
+// takes one off it and fails as an exhausted device would, without calling
+// cudaMalloc.
+std::atomic<int32_t> g_fail_allocs{0};
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  int32_t k = g_fail_allocs.load();
+  while (k > 0)
+    if (g_fail_allocs.compare_exchange_weak(k, k - 1)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
 #define BY_CU(x)                                                                    \
   do {                                                                              \
     cudaError_t e_ = (x);                                                           \
@@ -837,7 +849,7 @@ int bysdf_create_materials(const bysdf_material_desc* desc, int32_t n, void* str
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, M->device);
   M->smem_optin = (size_t)optin;
-  if ((e = cudaMalloc(&M->d_table, host.size())) != cudaSuccess)
+  if ((e = dev_alloc(reinterpret_cast<void**>(&M->d_table), host.size())) != cudaSuccess)
     return cleanup(fail(BYSDF_E_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
   if ((e = cudaMemcpyAsync(M->d_table, host.data(), host.size(), cudaMemcpyHostToDevice, st)) !=
           cudaSuccess ||
@@ -986,7 +998,9 @@ int bysdf_host_pipeline_create(const bysdf_materials* m, int64_t chunk, int with
     return fail(BYSDF_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&p->dev, bysdf_host_pipeline::kSlots * p->slot_bytes)) != cudaSuccess) return bad(e, "cudaMalloc");
+  if ((e = dev_alloc(reinterpret_cast<void**>(&p->dev), bysdf_host_pipeline::kSlots * p->slot_bytes)) !=
+      cudaSuccess)
+    return bad(e, "cudaMalloc");
   int dev = 0, pitch = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
       (e = cudaDeviceGetAttribute(&pitch, cudaDevAttrMaxPitch, dev)) != cudaSuccess)
@@ -1465,6 +1479,12 @@ int bysdf_noalloc_error(void* stream, uint32_t* err) {
 int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls) {
   if (!m) return fail(BYSDF_E_ARG, "materials is NULL");
   m->test_stall_polls = polls;
+  return BYSDF_OK;
+}
+
+int bysdf_test_fail_allocations(int32_t count) {
+  if (count < 0) return fail(BYSDF_E_ARG, "count < 0");
+  g_fail_allocs.store(count);
   return BYSDF_OK;
 }
 

@@ -80,6 +80,15 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bysdf_workspace_error(None, None, C.byref(err)) == -1
 
 
+def test_allocation_failure_hook_arguments(lib):
+    # the hook itself is host-only: a negative count is refused, 0 switches
+    # it off (its effect on the allocating calls is a GPU test)
+    assert lib.bysdf_test_fail_allocations(-1) == -1
+    assert "count" in lib.bysdf_last_error().decode()
+    assert lib.bysdf_test_fail_allocations(3) == 0
+    assert lib.bysdf_test_fail_allocations(0) == 0
+
+
 def test_shard_bounds_cover_and_balance():
     for n in (0, 1, 7, 1000, 2 ** 24 + 3):
         for w in (1, 2, 3, 8):

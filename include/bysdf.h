@@ -471,7 +471,9 @@ int bysdf_eval_noalloc(const bysdf_materials* m, const bysdf_hits* hits, int64_t
  * it (each call clears it first): 0 = none; bit 0: a bounded wait on a
  * shared-memory table copy gave up (the records of the tiles that could not
  * be evaluated have status 4); bit 1: a copy was still in flight after a
- * second bounded wait.  Synchronises the stream, then clears the word. */
+ * second bounded wait; bit 2 (index-checking build only, libbysdf_bounds.so
+ * built with -DBYSDF_DEBUG_BOUNDS): an index checked on the device was out
+ * of range and was clamped.  Synchronises the stream, then clears the word. */
 int bysdf_workspace_error(const void* workspace, void* stream, uint32_t* err);
 
 /* The error word of bysdf_eval_noalloc's fixed scratch on the current

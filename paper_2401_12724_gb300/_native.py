@@ -106,8 +106,13 @@ OP_EVAL, OP_SAMPLE, OP_PDF, OP_FUSED, OP_BACKWARD = range(5)
 NPARAM, NPARAM_EXT = 8, 15
 
 
+def bounds_checks() -> bool:
+    """BYSDF_BOUNDS_CHECKS=1 selects the index-checking build of the library."""
+    return os.environ.get("BYSDF_BOUNDS_CHECKS") == "1"
+
+
 def lib_path() -> str:
-    return _build.LIB_PATH
+    return _build.BOUNDS_LIB_PATH if bounds_checks() else _build.LIB_PATH
 
 
 def load(build_if_missing: bool = True):
@@ -119,7 +124,7 @@ def load(build_if_missing: bool = True):
             return _lib
         path = lib_path()
         if build_if_missing:
-            _build.build()
+            _build.build(bounds=bounds_checks())
         if not os.path.exists(path):
             raise RuntimeError(f"libbysdf not built: {path} is missing")
         L = C.CDLL(path)

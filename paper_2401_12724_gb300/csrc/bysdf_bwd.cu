@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = 0.f;
     for (int64_t i = begin + lane; i < end; i += 32) {
+      if (!bounds_ok(i >= 0 && i < a.n)) continue;
       Record q;
       load_record(a, i, true, false, q);
       // one call site of the (large, dual-number) record body for both
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
                              [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane,
                                  int) {
     for (int64_t i = begin + lane; i < end; i += 32) {
+      if (!bounds_ok(i >= 0 && i < a.n)) continue;
       Record q;
       load_record(a, i, true, false, q);
       const uint8_t* tb;

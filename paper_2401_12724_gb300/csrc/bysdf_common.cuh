@@ -299,6 +299,43 @@ __device__ __forceinline__ void xsincos_turns_fast(const DualF<N>& t, DualF<N>* 
 }
 template <class S> __device__ __forceinline__ S xmax0(const S& a) { return vf(a) < 0.f ? S(0.f) : a; }
 
+// ----------------------------------------------------------- index checks --
+// The index-checking build (-DBYSDF_DEBUG_BOUNDS, a separate library, the
+// stand-in for a memory checker): a checked index out of range sets bit 2
+// (ERR_BOUNDS) of the launch's error word and is clamped, so the access
+// stays in bounds.  Each kernel that reaches a check stores the word's
+// address (or NULL) in g_bounds_word before any check runs.  Compiled out of
+// the product build.
+enum : uint32_t { ERR_BOUNDS = 4u };
+#ifdef BYSDF_DEBUG_BOUNDS
+__shared__ unsigned long long* g_bounds_word;
+__device__ __forceinline__ void bounds_fail() {
+  if (g_bounds_word) atomicOr(g_bounds_word, (unsigned long long)ERR_BOUNDS);
+}
+#define BY_BOUNDS(ok, fix) \
+  do {                     \
+    if (!(ok)) {           \
+      bounds_fail();       \
+      fix;                 \
+    }                      \
+  } while (0)
+#else
+#define BY_BOUNDS(ok, fix) \
+  do {                     \
+  } while (0)
+#endif
+// the check as a value: false (after recording it) when the index is out of
+// range, so the caller can skip the access; always true in the product build
+__device__ __forceinline__ bool bounds_ok(bool ok) {
+#ifdef BYSDF_DEBUG_BOUNDS
+  if (!ok) bounds_fail();
+  return ok;
+#else
+  (void)ok;
+  return true;
+#endif
+}
+
 // ----------------------------------------------------------------- vectors --
 template <class S>
 struct V3 {

@@ -6,6 +6,11 @@ namespace bysdf {
 
 template <int OP>
 __global__ void __launch_bounds__(256, 2) k_plain(const KArgs a, int mat, int64_t begin, int64_t end) {
+#ifdef BYSDF_DEBUG_BOUNDS
+  // no workspace here: failed checks only clamp
+  if (threadIdx.x == 0) g_bounds_word = nullptr;
+  __syncthreads();
+#endif
   const int64_t i = begin + (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (i >= end) return;
   const MatDev* m = reinterpret_cast<const MatDev*>(a.table + (size_t)mat * a.stride);

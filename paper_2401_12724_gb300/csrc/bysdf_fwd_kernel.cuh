@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
       }
       if (e == 0xffffffffu) continue;
       const int64_t i = begin + (e & 0xffu);
+      if (!bounds_ok(i >= begin && i < end)) continue;
       Record q;
       load_record(a, i, (OP & (OPF_EVAL | OPF_PDF)) != 0, (OP & OPF_SAMPLE) != 0, q);
       const MatDev* m;
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_forward(const KArgs a) {
       } else {
         q.mat = a.mat_id ? __ldcg(a.mat_id + i) : 0;
         const int mm = (q.mat >= 0 && q.mat < a.n_mat) ? q.mat : 0;
+        if (!bounds_ok((size_t)mm * a.sstride + a.stride <= (size_t)a.order_off)) continue;
         m = reinterpret_cast<const MatDev*>(smem + (size_t)mm * a.sstride);
       }
       // two plies side by side in the trace when registers allow (<= 128)

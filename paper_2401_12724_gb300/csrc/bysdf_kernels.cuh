@@ -400,6 +400,10 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
                                                 Body&& body) {
   static_assert(BLOCK >= 64 && BLOCK % 32 == 0, "thread 32 claims the tile word");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#ifdef BYSDF_DEBUG_BOUNDS
+  if (threadIdx.x == 0) g_bounds_word = &a.ctl->err_word;
+  __syncthreads();
+#endif
   uint64_t* stall = bars + BLOCK / 32;
   const uint32_t limit = a.wait_limit ? a.wait_limit : kWaitLimit;
   __shared__ int s_ok;
@@ -451,6 +455,17 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
   }
   const int64_t n_tiles = a.mode == MODE_SORTED ? (int64_t)__ldg(a.tile_start + a.n_mat)
                                                 : a.n_tiles;
+#ifdef BYSDF_DEBUG_BOUNDS
+  {
+    // the staged tables (all of them, or one slot per warp) lie inside the
+    // launch's dynamic shared memory
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const size_t need = a.mode == MODE_ALL_SMEM ? (size_t)a.n_mat * a.sstride
+                                                : (size_t)(BLOCK / 32) * a.stride;
+    if (threadIdx.x == 0) BY_BOUNDS(need <= dyn, (void)0);
+  }
+#endif
   uint8_t* slot = smem + (size_t)warp * a.stride;
   uint32_t parity = 0;
   int cur = -1;
@@ -483,6 +498,7 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
         if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid;
       }
       mat = lo;
+      BY_BOUNDS(mat >= 0 && mat < a.n_mat, mat = 0);
       // offsets outside [0, n] are clamped: no access outside the records
       int64_t s0 = __ldg(a.seg + mat), s1 = __ldg(a.seg + mat + 1);
       s0 = s0 < 0 ? 0 : s0;
@@ -510,6 +526,7 @@ __device__ __forceinline__ void persistent_loop(const KArgs& a, uint8_t* smem, u
         }
       }
     }
+    BY_BOUNDS(begin >= 0 && end <= a.n && begin <= end, begin = end = 0);
     if (aborted) {
       abort_tile(a, begin, end, lane);
       continue;

@@ -153,6 +153,7 @@ __device__ __forceinline__ void fiber_lookup(const float2* map, int T, const S& 
   const S f = tau - fl;
   int i0 = (int)fl;
   i0 = i0 < 0 ? i0 + T : (i0 >= T ? i0 - T : i0);
+  BY_BOUNDS(i0 >= 0 && i0 < T, i0 = 0);
   const int i1 = i0 + 1 == T ? 0 : i0 + 1;
   const float2 t0 = map[i0], t1 = map[i1];
   *delta = t0.x + f * (t1.x - t0.x);
@@ -195,7 +196,9 @@ __device__ __forceinline__ void migration_maps(const MatDev& m, const float2* ma
   }
   const uint8_t* tab = mig_table(m);
   auto pick = [&](int sg, const float2** p, S* wk) {
-    const int k = tab[sg];
+    BY_BOUNDS(sg >= 0 && sg < kMigPeriod, sg = 0);
+    int k = tab[sg];
+    BY_BOUNDS(k < m.mig_maps, k = 0);
     if (k == 0) {
       *p = map0;
       *wk = w0;

@@ -500,6 +500,16 @@ int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls);
  * Process-wide.  Returns BYSDF_E_ARG for count < 0. */
 int bysdf_test_fail_allocations(int32_t count);
 
+/* Test hook of the float path's own approximations (no counterpart in the
+ * paper): out[i] = f(x[i], y[i]) for fn 0 the polynomial atan2(y, x) of the
+ * kernels, 1 CUDA's atan2f(y, x), 2 / 3 the sine / cosine the kernels take
+ * of the fiber normal's deviation, 4 / 5 CUDA's sinf / cosf; computed in a
+ * unit built with the kernels' flags.  x, y (fn 0 and 1 only), out: device
+ * arrays of n floats.  Asynchronous on stream; BYSDF_E_ARG on a bad fn, n or
+ * pointer. */
+int bysdf_test_math(int32_t fn, const float* x, const float* y, int64_t n, float* out,
+                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ SYMBOLS = [
     ("bysdf_noalloc_error", C.c_int, [P, C.POINTER(C.c_uint32)]),
     ("bysdf_test_stall_table_waits", C.c_int, [P, C.c_uint32]),
     ("bysdf_test_fail_allocations", C.c_int, [C.c_int32]),
+    ("bysdf_test_math", C.c_int, [C.c_int32, P, P, C.c_int64, P, P]),
     ("bysdf_host_pipeline_create", C.c_int, [P, C.c_int64, C.c_int, C.POINTER(P)]),
     ("bysdf_host_pipeline_destroy", C.c_int, [P]),
     ("bysdf_eval_sample_pdf_host", C.c_int,

@@ -1482,6 +1482,16 @@ int bysdf_test_stall_table_waits(bysdf_materials* m, uint32_t polls) {
   return BYSDF_OK;
 }
 
+int bysdf_test_math(int32_t fn, const float* x, const float* y, int64_t n, float* out,
+                    void* stream) {
+  if (fn < 0 || fn > 5) return fail(BYSDF_E_ARG, "fn outside [0, 5]");
+  if (n < 0) return fail(BYSDF_E_ARG, "n < 0");
+  if (n > 0 && (!x || !out || ((fn == 0 || fn == 1) && !y)))
+    return fail(BYSDF_E_ARG, "NULL argument");
+  BY_CU(launch_test_math(fn, x, y, n, out, reinterpret_cast<cudaStream_t>(stream)));
+  return BYSDF_OK;
+}
+
 int bysdf_test_fail_allocations(int32_t count) {
   if (count < 0) return fail(BYSDF_E_ARG, "count < 0");
   g_fail_allocs.store(count);

@@ -238,7 +238,9 @@ BY_DF xlog(const DualF<N>& a) { return dchain(a, logf(a.v), 1.0f / a.v); }
 // |y|) in [0, 1], atan(a) = a P(a^2) with P of degree 8 (coefficients fitted
 // here by weighted least squares on Chebyshev nodes of [0, 1]; maximum
 // error 5e-8 rad before rounding), then the octant's reflections.  Absolute
-// error a few 1e-7 rad, as the library's atan2f, at a quarter of its cost.
+// error a few 1e-7 rad, as the library's atan2f, at a quarter of its cost,
+// for arguments below 2^126 in magnitude (the approximate division of the
+// ratio returns 0 beyond; the kernels pass components of unit vectors).
 // atan2(0, 0) = 0.
 __device__ __forceinline__ float xatan2(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
@@ -267,11 +269,36 @@ __device__ __forceinline__ DualF<N> xatan2(const DualF<N>& y, const DualF<N>& x)
   for (int k = 0; k < N; ++k) r.d[k] = (x.v * y.d[k] - y.v * x.d[k]) * inv;
   return r;
 }
-__device__ __forceinline__ void xsincos(float x, float* s, float* c) { sincosf(x, s, c); }
+// Sine and cosine of an angle of at most pi/2 in magnitude (the fiber
+// normal's deviation from the ply normal): the Taylor series of sin to
+// x^13 / 13! and of cos to x^14 / 14!, in Horner form in x^2.  The first
+// omitted terms are below 7e-10 on [-pi/2, pi/2], so the error is the
+// evaluation's float rounding (a few 1e-8 absolute; cos keeps an absolute,
+// not a relative, bound next to pi/2).  Larger arguments take sincosf.
+__device__ __forceinline__ void xsincos(float x, float* s, float* c) {
+  if (!(fabsf(x) <= 1.57079637f)) {
+    sincosf(x, s, c);
+    return;
+  }
+  const float x2 = x * x;
+  float ps = fmaf(x2, 1.6059044e-10f, -2.5052108e-8f);   // 1/13!, -1/11!
+  ps = fmaf(x2, ps, 2.7557319e-6f);                       // 1/9!
+  ps = fmaf(x2, ps, -1.9841270e-4f);                      // -1/7!
+  ps = fmaf(x2, ps, 8.3333333e-3f);                       // 1/5!
+  ps = fmaf(x2, ps, -0.16666667f);                        // -1/3!
+  float pc = fmaf(x2, -1.1470746e-11f, 2.0876757e-9f);   // -1/14!, 1/12!
+  pc = fmaf(x2, pc, -2.7557319e-7f);                      // -1/10!
+  pc = fmaf(x2, pc, 2.4801587e-5f);                       // 1/8!
+  pc = fmaf(x2, pc, -1.3888889e-3f);                      // -1/6!
+  pc = fmaf(x2, pc, 4.1666668e-2f);                       // 1/4!
+  pc = fmaf(x2, pc, -0.5f);                               // -1/2!
+  *s = fmaf(x * x2, ps, x);
+  *c = fmaf(x2, pc, 1.0f);
+}
 template <int N>
 __device__ __forceinline__ void xsincos(const DualF<N>& x, DualF<N>* s, DualF<N>* c) {
   float sv, cv;
-  sincosf(x.v, &sv, &cv);
+  xsincos(x.v, &sv, &cv);
   *s = dchain(x, sv, cv);
   *c = dchain(x, cv, -sv);
 }

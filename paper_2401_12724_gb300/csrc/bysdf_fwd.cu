@@ -68,4 +68,32 @@ cudaError_t launch_plain(int op, const KArgs& a, int mat, int64_t begin, int64_t
   return cudaGetLastError();
 }
 
+// The float path's approximations evaluated on given arguments, beside the
+// CUDA functions they stand in for, in a unit built with the forward's
+// flags (approximate division and square root, denormals flushed): 0
+// xatan2(y, x), 1 atan2f(y, x), 2 / 3 sine / cosine of xsincos(x), 4 / 5
+// sinf(x) / cosf(x).
+__global__ void k_test_math(int fn, const float* x, const float* y, int64_t n, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float a = x[i], b = y ? y[i] : 0.f;
+  float r = 0.f, s, c;
+  switch (fn) {
+    case 0: r = xatan2(b, a); break;
+    case 1: r = atan2f(b, a); break;
+    case 2: xsincos(a, &s, &c); r = s; break;
+    case 3: xsincos(a, &s, &c); r = c; break;
+    case 4: r = sinf(a); break;
+    case 5: r = cosf(a); break;
+  }
+  out[i] = r;
+}
+
+cudaError_t launch_test_math(int fn, const float* x, const float* y, int64_t n, float* out,
+                             cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_test_math<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fn, x, y, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace bysdf

@@ -38,5 +38,8 @@ cudaError_t backward_occupancy(int block, int occ, int kind, size_t smem, int* c
 cudaError_t set_dirgrad_smem_limit(int block, size_t smem);
 cudaError_t dirgrad_occupancy(int block, size_t smem, int* ctas);
 cudaError_t launch_dirgrad(const KArgs& a, int block, int grid, size_t smem, cudaStream_t st);
+// test hook: the float path's own approximations beside CUDA's functions
+cudaError_t launch_test_math(int fn, const float* x, const float* y, int64_t n, float* out,
+                             cudaStream_t st);
 
 }  // namespace bysdf

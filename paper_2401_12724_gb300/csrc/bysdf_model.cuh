@@ -86,22 +86,22 @@ __device__ __forceinline__ S frac_prod_s(const S& k, float hi, float lo, float v
 // ------------------------------------------------------------ validation --
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
 
+// The checks are combined without early exits (one branch per record, not
+// one per input: 1.7% of the fused kernel's time).  A direction is unit
+// within 1e-3 only if its components are finite (a non-finite component
+// makes the squared norm NaN or infinite).
 __device__ __forceinline__ bool unit_ok(const float* w) {
-  if (!finitef(w[0]) || !finitef(w[1]) || !finitef(w[2])) return false;
   const float nn = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   return fabsf(nn - 1.0f) <= 1e-3f;
 }
 // Inputs every op needs: (h, u, v, omega_i, material id, ratio).
 __device__ __forceinline__ bool base_valid(const Record& q, int n_mat, bool has_ratio) {
-  if (!finitef(q.h) || !finitef(q.u) || !finitef(q.v)) return false;
-  if (fabsf(q.h) > 1.0f) return false;
-  if (!unit_ok(q.wi)) return false;
-  if (q.mat < 0 || q.mat >= n_mat) return false;
-  if (has_ratio && !(q.ratio >= 0.0f && finitef(q.ratio))) return false;
-  return true;
+  const bool ratio_ok = !has_ratio || (q.ratio >= 0.0f && q.ratio < INFINITY);
+  return (fabsf(q.h) <= 1.0f) & finitef(q.u) & finitef(q.v) & unit_ok(q.wi) &
+         (q.mat >= 0) & (q.mat < n_mat) & ratio_ok;
 }
 __device__ __forceinline__ bool u_valid(const Record& q) {
-  return q.u0 >= 0.0f && q.u0 < 1.0f && q.u1 >= 0.0f && q.u1 < 1.0f;
+  return (q.u0 >= 0.0f) & (q.u0 < 1.0f) & (q.u1 >= 0.0f) & (q.u1 < 1.0f);
 }
 __device__ __forceinline__ bool record_valid(const Record& q, int n_mat, bool need_wo,
                                              bool has_ratio, bool need_u) {
@@ -483,10 +483,19 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     const P b = qx * wx + qy * wy;
     const P perp = qx * wy - qy * wx;
     const P disc = (Rp - perp) * (Rp + perp);
-    if (vf(disc) > 0.f) {
-      const P sq = xsqrt(disc);
-      const P s2 = sq - b;
-      if (vf(s2) > 0.f) occ = occ + (s2 - xmax0(-b - sq));
+    if constexpr (is_dual<P>::value) {
+      if (vf(disc) > 0.f) {
+        const P sq = xsqrt(disc);
+        const P s2 = sq - b;
+        if (vf(s2) > 0.f) occ = occ + (s2 - xmax0(-b - sq));
+      }
+    } else {
+      // predicated (no branch): the chord from its near end max(-b - sq, 0)
+      // to its far end s2 = sq - b, where the ray meets the disc ahead
+      const float sq = sqrtf(fmaxf(disc, 0.f));
+      const float s2 = sq - b;
+      const float chord = s2 - fmaxf(-b - sq, 0.f);
+      occ += (disc > 0.f && s2 > 0.f) ? chord : 0.f;
     }
   }
   const S occ_all = widen<S>(occ) * m.inv_2Rp + of;

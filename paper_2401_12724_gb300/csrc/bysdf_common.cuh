@@ -314,15 +314,19 @@ __device__ __forceinline__ void xsincos_turns(const DualF<N>& t, DualF<N>* s, Du
   *c = dchain(t, cv, -2.0f * kPi * sv);
 }
 // sin and cos of 2 pi t for the small per-step phase advances of the ply
-// trace: the float path reduces t to [-1/2, 1/2] exactly and uses the
-// hardware approximations (absolute error ~5e-7); duals use the exact form.
+// trace: t is reduced to [-1/2, 1/2] exactly and the hardware
+// approximations are taken (absolute error ~5e-7); the tangents follow from
+// those values.
 __device__ __forceinline__ void xsincos_turns_fast(float t, float* s, float* c) {
   const float r = t - rintf(t);
   __sincosf((2.0f * kPi) * r, s, c);
 }
 template <int N>
 __device__ __forceinline__ void xsincos_turns_fast(const DualF<N>& t, DualF<N>* s, DualF<N>* c) {
-  xsincos_turns(t, s, c);
+  float sv, cv;
+  xsincos_turns_fast(t.v, &sv, &cv);
+  *s = dchain(t, sv, 2.0f * kPi * cv);
+  *c = dchain(t, cv, -2.0f * kPi * sv);
 }
 template <class S> __device__ __forceinline__ S xmax0(const S& a) { return vf(a) < 0.f ? S(0.f) : a; }
 

@@ -410,8 +410,14 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   bool grazed = false;
 #pragma unroll 1
   for (int i = 0; i < n_upd; ++i) {
+    // the dual pass traces its ply's N_it updates like the float pass: the
+    // hardware sin/cos, the last update correctly rounded
     P sd, cd;
-    xsincos_turns(kp * (kappa * best_t), &sd, &cd);
+    if (i + 1 < n_upd) {
+      xsincos_turns_fast(kp * (kappa * best_t), &sd, &cd);
+    } else {
+      xsincos_turns(kp * (kappa * best_t), &sd, &cd);
+    }
     best_c = ck * cd - sk * sd;
     best_s = sk * cd + ck * sd;
     best_cx = Rc * best_c;

@@ -121,31 +121,75 @@ __global__ void k_reduce_partials(const KArgs a) {
   }
 }
 
+enum { DD_WI = 0, DD_WO = 3, NDD = 6 };
+
+// A shading state with omega_i's three tangents as one with all six (the
+// omega_o tangents zero).
+template <class D, class DI>
+__device__ __forceinline__ D widen_di(const DI& x) {
+  D r(x.v);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r.d[DD_WI + k] = x.d[k];
+  return r;
+}
+template <class D, class DI>
+__device__ __forceinline__ V3<D> widen_di3(const V3<DI>& x) {
+  return mk3<D>(widen_di<D>(x.x), widen_di<D>(x.y), widen_di<D>(x.z));
+}
+template <class D, class DI>
+__device__ __forceinline__ Shade<D> widen_shade(const Shade<DI>& x) {
+  Shade<D> r;
+  r.t = widen_di3<D>(x.t);
+  r.b = widen_di3<D>(x.b);
+  r.n = widen_di3<D>(x.n);
+  r.wi = widen_di3<D>(x.wi);
+  r.mui = widen_di<D>(x.mui);
+  r.g = widen_di<D>(x.g);
+  r.fr = widen_di<D>(x.fr);
+  r.at = x.at;
+  r.ab = x.ab;
+  r.at_free = x.at_free;
+  r.ab_free = x.ab_free;
+  r.body_x0 = widen_di<D>(x.body_x0);
+  r.body_y0 = widen_di<D>(x.body_y0);
+  r.ni_sy = x.ni_sy;
+  r.tt_ok = x.tt_ok;
+  r.iy = widen_di3<D>(x.iy);
+  r.by = widen_di3<D>(x.by);
+  r.ny = widen_di3<D>(x.ny);
+  r.tx = widen_di<D>(x.tx);
+  r.tau = widen_di<D>(x.tau);
+  return r;
+}
+
 // Direction vector-Jacobian products of one record: sum_c g_c df_c/dwi and
 // df_c/dwo.  Tangents 0..2: wi, 3..5: wo.  The material's helix angles carry
 // no tangent here; the float pre-pass of the geometry picks each node's ply.
-enum { DD_WI = 0, DD_WO = 3, NDD = 6 };
 __device__ __forceinline__ void dirgrad_record(const KArgs& a, const MatDev& m,
                                                const float2* map, int64_t i, Record& q,
                                                float gwi[3], float gwo[3]) {
   typedef DualF<NDD> D;
+  typedef DualF<3> DI;   // omega_i's tangents alone
 #pragma unroll
   for (int c = 0; c < 3; ++c) gwi[c] = gwo[c] = 0.f;
   if (!record_valid(q, a.n_mat, true, a.ratio != nullptr, false)) return;
-  const MatVars<D> mv = mat_vars<D>(m, false);
-  V3<D> wi = lift3<D>(q.wi[0], q.wi[1], q.wi[2]);
+  // omega_o enters only the lobes: the geometry and the shading frame carry
+  // omega_i's three tangents, and are widened to all six for the lobes
+  const MatVars<DI> mv = mat_vars<DI>(m, false);
+  V3<DI> wi = lift3<DI>(q.wi[0], q.wi[1], q.wi[2]);
+  wi.x.d[0] = 1.f;
+  wi.y.d[1] = 1.f;
+  wi.z.d[2] = 1.f;
+  Geo<DI> G;
+  geometry_k<1, DI, DI>(m, map, mv, q, wi, G);
+  if (G.status != ST_OK) return;
+  Shade<DI> si;
+  make_shade(m, mv, G, wi, si);
+  const Shade<D> s = widen_shade<D>(si);
   V3<D> wo = lift3<D>(q.wo[0], q.wo[1], q.wo[2]);
-  wi.x.d[DD_WI + 0] = 1.f;
-  wi.y.d[DD_WI + 1] = 1.f;
-  wi.z.d[DD_WI + 2] = 1.f;
   wo.x.d[DD_WO + 0] = 1.f;
   wo.y.d[DD_WO + 1] = 1.f;
   wo.z.d[DD_WO + 2] = 1.f;
-  Geo<D> G;
-  geometry_k<1, D, D>(m, map, mv, q, wi, G);
-  if (G.status != ST_OK) return;
-  Shade<D> s;
-  make_shade(m, mv, G, wi, s);
   LobeVals<D> L;
   eval_lobes(m, s, wo, L);
   const int64_t n = a.n;

@@ -9,7 +9,6 @@ computed with the kernels' build flags):
 * the sine and cosine of the fiber normal's deviation (Taylor polynomials to
   degree 13 / 14 on [-pi/2, pi/2], sincosf beyond) against sinf / cosf and
   float64."""
-import ctypes as C
 
 import numpy as np
 import pytest

@@ -260,7 +260,8 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
                                               const K& wx, const K& wy, const S& s0v,
                                               const S& c0v, const S& phase_f_v,
                                               NodeGeo<S>& out, int only_ply = -1,
-                                              int ni_known = 0, bool trace_only = false) {
+                                              int ni_known = 0, bool trace_only = false,
+                                              bool coarse = false) {
   const float Rp = m.Rp, Rc = m.Rc;
   out.hit = false;
   out.ni = 0;
@@ -413,7 +414,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
     // the dual pass traces its ply's N_it updates like the float pass: the
     // hardware sin/cos, the last update correctly rounded
     P sd, cd;
-    if (i + 1 < n_upd) {
+    if (i + 1 < n_upd || coarse) {
       xsincos_turns_fast(kp * (kappa * best_t), &sd, &cd);
     } else {
       xsincos_turns(kp * (kappa * best_t), &sd, &cd);
@@ -599,8 +600,10 @@ __device__ __forceinline__ void geometry_k(const MatDev& m, const float2* map,
       node_geometry<S, PLIES, K>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v,
                                  phase_f_v, nd, pick.ply, pick.ni);
     } else {
+      // a node of several: its last update takes the hardware sin/cos too
+      // (the aggregate averages the nodes' frames)
       node_geometry<S, PLIES, K>(m, map, mv, X0x, X0y, ex, ey, q.v, kappa, wx, wy, s0v, c0v,
-                                 phase_f_v, nd);
+                                 phase_f_v, nd, -1, 0, false, !near);
     }
     if (!nd.hit) continue;
     nhit += 1;

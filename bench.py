@@ -55,8 +55,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="2f23a49e40ba4f532435b872397347d4bdd126d3c374a0cd10d1ed914201525b",
-                       bytes_per_record=82.42,
+TRAFFIC_CAPTURE = dict(sources_sha256="84933bb9cb907fc5ca03b1ca1b44dcabb40671aa8ced47a2ac356edfa40b8b0f",
+                       bytes_per_record=82.49,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

@@ -478,7 +478,17 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   const V3<S> nps = widen3<S>(np);
   out.tf = widen3<S>(tp) * mv.cos_af + widen3<S>(ep) * mv.sin_af;
   S sd, cd;
-  xsincos(delta, &sd, &cd);
+  if constexpr (!is_dual<S>::value) {
+    // a node of a multi-node aggregate: the hardware sin/cos (|delta| <=
+    // pi/2, absolute error ~5e-7)
+    if (coarse) {
+      __sincosf(delta, &sd, &cd);
+    } else {
+      xsincos(delta, &sd, &cd);
+    }
+  } else {
+    xsincos(delta, &sd, &cd);
+  }
   out.nf = nps * cd + cross(out.tf, nps) * sd;
   // Sec. 4.1.4: ply shadowing by the in-plane chords through the other
   // plies of this cross-section; fiber shadowing from the map

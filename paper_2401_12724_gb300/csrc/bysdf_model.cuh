@@ -445,7 +445,7 @@ __device__ __forceinline__ void node_geometry(const MatDev& m, const float2* map
   const P dz = kappa * best_t;
   out.x = mk3<S>(widen<S>(xx), widen<S>(xy), widen<S>(v + dz));
   const P dx = xx - best_cx, dy = xy - best_cy;
-  const P inv_dl = 1.0f / xsqrt(dx * dx + dy * dy);
+  const P inv_dl = xrsqrt(dx * dx + dy * dy);
   const V3<P> np = mk3<P>(dx * inv_dl, dy * inv_dl, P(0.f));
   const P wp = (2.0f * kPi) * kp;
   const V3<P> traw = mk3<P>(-(wp * xy), wp * xx, P(1.f));
@@ -696,7 +696,7 @@ __device__ __forceinline__ V3<S> vndf_sample(const V3<S>& w, float at, float ab,
   const S lensq = V.x * V.x + V.y * V.y;
   V3<S> T1 = lift3<S>(1.f, 0.f, 0.f);
   if (vf(lensq) > 0.f) {
-    const S il = 1.0f / xsqrt(lensq);
+    const S il = xrsqrt(lensq);
     T1 = mk3<S>(-(V.y * il), V.x * il, S(0.f));
   }
   const V3<S> T2 = cross(V, T1);
@@ -801,7 +801,7 @@ __device__ __forceinline__ void make_shade(const MatDev& m, const MatVars<S>& mv
   const S disc = xmax0(bq * bq - a * c);
   const S sy = xmax0((xsqrt(disc) - bq) / a);
   const S yx = G.x.x + din.x * sy, yy = G.x.y + din.y * sy;
-  const S il = 1.0f / xsqrt(yx * yx + yy * yy);
+  const S il = xrsqrt(yx * yx + yy * yy);
   s.ny = mk3<S>(yx * il, yy * il, S(0.f));
   s.by = mk3<S>(s.ny.y, -s.ny.x, S(0.f));  // n_y x z
   s.iy = -din;

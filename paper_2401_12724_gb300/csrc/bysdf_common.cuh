@@ -234,15 +234,15 @@ BY_DF xrsqrt(const DualF<N>& a) {
   const float r = rsqrtf(a.v);
   return dchain(a, r, -0.5f * r * r * r);
 }
-// float path: hardware exp2 / log2 based (relative error ~1e-7 for the
-// arguments here, |x| < ~20); duals keep the library versions
+// hardware exp2 / log2 based (relative error ~1e-7 for the arguments here,
+// |x| < ~20), for floats and for the values of duals alike
 __device__ __forceinline__ float xexp(float x) { return __expf(x); }
 BY_DF xexp(const DualF<N>& a) {
-  const float e = expf(a.v);
+  const float e = __expf(a.v);
   return dchain(a, e, e);
 }
 __device__ __forceinline__ float xlog(float x) { return __logf(x); }
-BY_DF xlog(const DualF<N>& a) { return dchain(a, logf(a.v), 1.0f / a.v); }
+BY_DF xlog(const DualF<N>& a) { return dchain(a, __logf(a.v), 1.0f / a.v); }
 // atan2 for the float path: the octant's ratio a = min(|x|, |y|) / max(|x|,
 // |y|) in [0, 1], atan(a) = a P(a^2) with P of degree 8 (coefficients fitted
 // here by weighted least squares on Chebyshev nodes of [0, 1]; maximum

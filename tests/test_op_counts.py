@@ -38,3 +38,14 @@ def test_reverse_sweep_cost_model(orc):
     assert count.adjoint(0, 0, 1, 0, 0) == (2, 1, 1)
     assert count.adjoint(0, 0, 0, 1, 0) == (1, 1, 1)
     assert count.adjoint(0, 0, 0, 0, 1) == (1, 1, 1)
+
+
+def test_oracle_rate_script_measures_every_workload(orc, monkeypatch):
+    # oracle/rates.py (the CPU reference rates of the measured table): one
+    # short pass per workload and thread count, on small samples
+    rates = _load("oracle/rates.py", "oracle_rates")
+    monkeypatch.setattr(rates, "workload_sample",
+                        lambda cfg, n, f=rates.workload_sample: f(cfg, min(n, 512)))
+    for cfg in (1, 4, 5):
+        r = rates.rate(cfg, 2, 1 << 9, 0.0)
+        assert r["records"] == 512 and r["records_per_s"] > 0 and r["threads"] == 2

@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_backward(const KArgs a) {
     float acc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = 0.f;
+    // rolled: one copy of the (large) record body
+#pragma unroll 1
     for (int64_t i = begin + lane; i < end; i += 32) {
       if (!bounds_ok(i >= 0 && i < a.n)) continue;
       Record q;
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_dirgrad(const KArgs a) {
   persistent_loop<BLOCK>(a, smem, bars,
                              [&](int64_t begin, int64_t end, int mat, uint8_t* slot, int lane,
                                  int) {
+#pragma unroll 1
     for (int64_t i = begin + lane; i < end; i += 32) {
       if (!bounds_ok(i >= 0 && i < a.n)) continue;
       Record q;

@@ -55,8 +55,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="0f67a3e3f7378291ffa5c5d006c316e8526fffcaf57b31ce843330de7d7d03fe",
-                       bytes_per_record=82.39,
+TRAFFIC_CAPTURE = dict(sources_sha256="02e683edc06472a3b5e8245316eef60f9572f13b2221e5b9ebda4d2cddeb9f84",
+                       bytes_per_record=82.44,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

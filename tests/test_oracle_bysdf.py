@@ -429,3 +429,36 @@ def test_l2_loss_is_multimodal_in_the_helix_angles(orc):
         d = np.diff(np.array(loss))
         minima = int(((d[:-1] < 0) & (d[1:] > 0)).sum())
         assert minima >= 3, (key, minima)
+
+
+def test_l2_loss_gradient_matches_finite_differences(orc, monkeypatch):
+    # the objective of the fused L2 pass, L = sum_i w_i sum_c (f_c - t_c)^2
+    # over the valid records, differentiated with the oracle's exact
+    # gradient at g = 2 w (f - t), against central differences of L itself
+    # (float64 descriptors so that the steps are not rounded away)
+    import oracle.oracle as O
+    monkeypatch.setattr(O, "_material", _material_f64(O))
+    m = mat(n_plies=3, ply_twist_deg=28.0, fiber_twist_deg=20.0, beta_deg=[12.0, 9.0],
+            albedo=[0.3, 0.6, 0.8], shadow_density=0.7)
+    rec = I.random_records(300, seed=47, wi_mode="cosine", v_max=3.0)
+    rng = np.random.default_rng(48)
+    f0, _, st = orc.eval_records([m], rec)
+    target = f0 * rng.uniform(0.6, 1.4, f0.shape)
+    w = rng.uniform(0.5, 1.5, 300) * (st == 0)
+
+    def loss(mm):
+        f, _, _ = orc.eval_records([mm], rec)
+        return float((w * ((f - target) ** 2).sum(0)).sum())
+
+    g = 2.0 * w * (f0 - target)
+    grad, _ = orc.grad_records([m], rec, g)
+    checked = 0
+    for k in range(8):
+        eps = 1e-6
+        fd = (loss(perturbed(m, k, eps)) - loss(perturbed(m, k, -eps))) / (2 * eps)
+        fd2 = (loss(perturbed(m, k, 2 * eps)) - loss(perturbed(m, k, -2 * eps))) / (4 * eps)
+        if abs(fd - fd2) > 1e-5 * (1 + abs(fd)):
+            continue              # a record on a branch within the step
+        checked += 1
+        np.testing.assert_allclose(grad[0, k], fd, rtol=1e-5, atol=1e-6)
+    assert checked >= 6

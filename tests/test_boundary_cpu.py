@@ -182,3 +182,24 @@ def test_bench_parity_report_counts_planted_errors():
     n_cmp = (n - 20) + (n - 1)                 # eval records both ok + sample records kept
     assert abs(r["within_tol"] - (n_cmp - 2) / n_cmp) < 1e-12
     assert 0.009 < r["rel_err_max"] < 0.011 and r["rel_err_p50"] < 1e-6
+
+
+def test_bench_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference: the FP64 oracle on the host cores, one JSON
+    # line with the contract's keys (runs without a GPU)
+    import json
+    import sys
+    env = dict(os.environ, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "2", "--warmup", "1"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0

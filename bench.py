@@ -55,8 +55,8 @@ OPS = {
 # workload, per record; the records stream through once, so traffic scales
 # with the record count).  It is reported only while the kernel sources are
 # the ones captured (SHA-256 of FUSED_SOURCES).
-TRAFFIC_CAPTURE = dict(sources_sha256="02e683edc06472a3b5e8245316eef60f9572f13b2221e5b9ebda4d2cddeb9f84",
-                       bytes_per_record=82.44,
+TRAFFIC_CAPTURE = dict(sources_sha256="07f29fb7cc8d35a65bad24fce53f029eea1404be7ea8e7c308d8f21570f80e8a",
+                       bytes_per_record=82.51,
                        summary="profiles/k_forward_fused_eval-sample-pdf_8mat.md")
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (2 flops each)
 XU_LANES_PER_SM = 16      # special-function (MUFU) lanes per SM

@@ -138,10 +138,10 @@ typedef struct bysdf_hits {
 /* Launch shape of the persistent kernels (chosen by bysdf_autotune). */
 typedef struct bysdf_launch_config {
   int32_t block;          /* threads per CTA: 128, 256 or 512               */
-  int32_t items;          /* records per lane per warp tile: 1, 2, 4 or 8; the
-                             forward calls take 1 for a batch of fewer tiles
-                             than the grid's resident warps, so that more
-                             warps get work                                  */
+  int32_t items;          /* records per lane per warp tile: 1, 2, 4 or 8
+                             (the backward also 16); a batch of fewer tiles
+                             than the grid's resident warps takes smaller
+                             tiles, so that more warps get work              */
   int32_t ctas_per_sm;    /* resident CTAs per SM the grid is sized for
                              (0: as many as fit)                             */
   int32_t occupancy;      /* register budget: 0 the default, 1 a tighter cap

@@ -360,12 +360,14 @@ int64_t max_tiles(int64_t n, int n_mat) { return (n + 31) / 32 + n_mat; }
 // pdf over 2^24 records; forward + backward over 2^24 material-sorted
 // records of 64 materials): 16 warps per SM in CTAs of 512; four records
 // per lane per warp tile for the forward calls (two or eight within 0.3%),
-// eight for the backward (per 2^24 records 2.35 ms, against 2.42 ms at four
-// and 3.10 ms at two).  bysdf_autotune refines them for a given record set.
+// sixteen for the backward (the fused L2 pass per 2^24 records 2.25 ms,
+// against 2.28 ms at eight, 2.53 ms at four and 3.12 ms at two, at the
+// kernels of their times).  bysdf_autotune refines them for a given record
+// set.
 bysdf_launch_config default_cfg(int op) {
   bysdf_launch_config c;
   c.block = 512;
-  c.items = op == BYSDF_OP_BACKWARD ? 8 : 4;
+  c.items = op == BYSDF_OP_BACKWARD ? 16 : 4;
   c.ctas_per_sm = 0;  // 0: as many as fit
   c.occupancy = 0;
   return c;
@@ -1399,8 +1401,9 @@ int bysdf_set_launch_config(bysdf_materials* m, int op, const bysdf_launch_confi
   if (op < 0 || op >= BYSDF_NOPS) return fail(BYSDF_E_ARG, "bad op");
   if (cfg->block != 128 && cfg->block != 256 && cfg->block != 512)
     return fail(BYSDF_E_ARG, "block must be 128, 256 or 512");
-  if (cfg->items != 1 && cfg->items != 2 && cfg->items != 4 && cfg->items != 8)
-    return fail(BYSDF_E_ARG, "items must be 1, 2, 4 or 8");
+  const bool items_ok = cfg->items == 1 || cfg->items == 2 || cfg->items == 4 ||
+                        cfg->items == 8 || (op == BYSDF_OP_BACKWARD && cfg->items == 16);
+  if (!items_ok) return fail(BYSDF_E_ARG, "items must be 1, 2, 4 or 8 (16 for the backward)");
   if (cfg->ctas_per_sm < 0) return fail(BYSDF_E_ARG, "ctas_per_sm < 0");
   if (cfg->occupancy != 0 && cfg->occupancy != 1) return fail(BYSDF_E_ARG, "occupancy must be 0 or 1");
   m->cfg[op] = *cfg;
@@ -1435,7 +1438,8 @@ int bysdf_autotune(bysdf_materials* m, int op, const bysdf_hits* hits, const flo
   bysdf_launch_config best_c = m->cfg[op];
   int rc = BYSDF_OK;
   for (int block : {128, 256, 512}) {
-    for (int items : {1, 2, 4, 8}) {
+    for (int items : {1, 2, 4, 8, 16}) {
+      if (items == 16 && op != BYSDF_OP_BACKWARD) continue;  // forward kernels: up to 8
       for (int occ_mode : {0, 1}) {
         if (occ_mode == 1 && block == 512) continue;
         bysdf_launch_config c{block, items, 0, occ_mode};
